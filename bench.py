@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: odd n verified per second (mink for every odd n of a range).
+
+Default workload (N=1): the range [2^40, 2^40 + 2^34), i.e. 2^33 odd n per
+step, sieved with every odd prime p <= isqrt(hi - 1) and scanned for the
+smallest k.  With N GPUs (torchrun) every rank verifies its own disjoint range
+of the same length (weak scaling, no data-path collective); the time is the
+maximum over ranks.
+
+`value` is device time: CUDA events on the library's stream around each step
+(inputs already on the device: a range needs only its two bounds), with L2
+flushed between steps.  `e2e` times the public blocking call with host
+buffers (descriptor upload, result download and host-side list sort inside).
+`--impl reference` times the CPU oracle (all host cores) on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2411_01964_gb300 import inputs  # noqa: E402
+
+METRIC = "odd n verified/s (min-k)"
+UNIT = "odd_n/s"
+
+WORKLOADS = {
+    "C1": inputs.C1,
+    "C2": inputs.C2,
+    "C3": inputs.C3,
+}
+WORKLOAD_NAMES = {
+    "C1": "plain single range [3, 2^24), primes <= 2^12",
+    "C2": "plain single range [2^40, 2^40+2^34), primes <= isqrt(hi-1) = 1056736",
+    "C3": "plain single range [2^50-2^36, 2^50), primes <= 2^25",
+}
+
+# Table 1 (Sec. 2): c_l = P(one of n-2^1..n-2^l squarefree), l = 1..6.
+C_ELL = [0.810569, 0.975870, 0.997851, 0.999860, 0.999993, 0.99999973]
+
+
+def odd_count(lo, hi):
+    nlo = max(lo, 3) | 1
+    return (hi - nlo + 1) // 2 if hi > nlo else 0
+
+
+def alu_ops_per_odd_n(hi: int) -> float:
+    """Algorithmic 32-bit integer operations per odd n of the word-parallel
+    method (one 32-bit word = 32 odd n):
+      stamp:  2 ops (pattern shift, AND) per stamped prime p in {3,5,7,11} + 1 store
+      strike: 2 ops (address, atomic AND) per struck bit, 32 * sum_{13<=p<=sqrt(hi)} 1/p^2 per word
+      scan:   2 loads, then 3 ops (shift, AND-NOT, popcount) per k step; a word
+              needs E = 1 + sum_k (1 - c_k^32) steps (c_k from Table 1)
+    """
+    import numpy as np
+    lim = math.isqrt(hi - 1)
+    sieve = np.ones(lim + 1, dtype=bool)
+    sieve[:2] = False
+    for i in range(2, math.isqrt(lim) + 1):
+        if sieve[i]:
+            sieve[i * i::i] = False
+    ps = np.nonzero(sieve)[0]
+    ps = ps[ps >= 13].astype(np.float64)
+    strikes_per_word = 32.0 * float(np.sum(1.0 / (ps * ps)))
+    e_steps = 1.0 + sum(1.0 - c ** 32 for c in C_ELL)
+    per_word = (2 * 4 + 1) + 2 * strikes_per_word + 2 + 3 * e_steps
+    return per_word / 32.0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    lo, hi = WORKLOADS[args.workload]
+    cores = os.cpu_count() or 1
+    sample = min(hi - lo, args.ref_sample)
+    slo, shi = lo, lo + sample
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.verify_range(slo, slo + min(sample, 1 << 26), threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.verify_range(slo, shi, threads=cores)
+        times.append(time.perf_counter() - t0)
+    n = odd_count(slo, shi)
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (integer ranges)",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "sample": f"[{slo}, {shi}) per step",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"odd n of [{slo}, {shi}) ({n} odd n) per step, all host cores"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "check": {"n_odd": r.n_odd, "hist_sum": sum(r.hist)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(lo: int, hi: int, seconds_target: float, max_sample: int) -> dict:
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # calibrate on a small piece, then size the sample for ~seconds_target
+    probe = min(hi - lo, 1 << 26)
+    t0 = time.perf_counter()
+    oracle.verify_range(lo, lo + probe, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    sample = int(probe * seconds_target / dt) & ~((1 << 20) - 1)
+    sample = max(probe, min(sample, hi - lo, max_sample))
+    t0 = time.perf_counter()
+    r = oracle.verify_range(lo, lo + sample, threads=cores)
+    dt = time.perf_counter() - t0
+    n = odd_count(lo, lo + sample)
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"odd n of [{lo}, {lo + sample}) ({n} odd n, {dt:.1f} s), all host cores",
+            "n_odd": r.n_odd}
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-sample", type=int, default=1 << 31)
+    ap.add_argument("--tile-log2", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--margin-log2", type=int, default=0)
+    ap.add_argument("--large-prime-min", type=int, default=0)
+    ap.add_argument("--range", default="", help="LO:HI overrides the workload's range (profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_2411_01964_gb300 import Verifier, binding as B
+
+    lo0, hi0 = WORKLOADS[args.workload]
+    if args.range:
+        lo0, hi0 = (int(x, 0) for x in args.range.split(":"))
+    length = hi0 - lo0
+    lo, hi = lo0 + rank * length, hi0 + rank * length  # this rank's shard
+    n_odd = odd_count(lo, hi)
+    # a dedicated stream: the library enqueues on it and the step events are
+    # recorded on it (never the legacy default stream, which a library-owned
+    # non-blocking stream would not order against)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    knobs = {k: v for k, v in (("tile_log2", args.tile_log2), ("threads", args.threads),
+                                 ("ctas_per_sm", args.ctas_per_sm), ("margin_log2", args.margin_log2),
+                                 ("large_prime_min", args.large_prime_min)) if v}
+    v = Verifier(max_hi=hi + 1, stream=stream.cuda_stream, **knobs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    # warm-up (and a first correctness glance: every odd n accounted for)
+    for _ in range(args.warmup):
+        v.launch_range(lo, hi)
+        r = v.fetch_range()
+    assert sum(r.hist) + r.fail_len == n_odd, "histogram does not cover the range"
+
+    B.sv_kernel_timing(v.ctx, True)
+    launches0 = v.kernel_launches()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush, outside the events
+        starts[i].record(stream)
+        v.launch_range(lo, hi)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = v.kernel_launches() - launches0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    tile_ms, tile_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["tile"])
+    bucket_ms, bucket_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["bucket_fill"])
+    B.sv_kernel_timing(v.ctx, False)
+    res = v.fetch_range()
+    assert sum(res.hist) + res.fail_len == n_odd
+
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n_odd * world * args.steps / (total_ms / 1e3)
+
+    # end to end: the blocking public call with host buffers
+    e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
+    rr = res
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        rr = v.verify_range(lo, hi)
+        a, b = v.last_transfer()
+        h2d += a
+        d2h += b
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = n_odd * world * e2e_steps / e2e_s if e2e_steps else None
+    assert rr.hist == res.hist
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = props.multi_processor_count * 128 * sm_max * 1e6  # int32 lane-ops/s
+    ops_per_n = alu_ops_per_odd_n(hi)
+    tile_avg_s = (tile_ms / max(tile_n, 1)) / 1e3
+    achieved = ops_per_n * n_odd / tile_avg_s
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (integer ranges; inputs are the range bounds)",
+        "config": {"workload": (f"custom range [{lo0}, {hi0})" if args.range else WORKLOAD_NAMES[args.workload]), "lo": lo0, "hi": hi0,
+                   "odd_n_per_gpu": n_odd, "parallelism": f"shards x{world}" if world > 1 else "1 GPU",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "tile_log2": v.config.tile_log2, "threads": v.config.threads,
+                   "margin_log2": v.config.margin_log2, "ctas_per_sm": v.config.ctas_per_sm,
+                   "large_prime_min": v.config.large_prime_min},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "int32 ops/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "tile_kernel (sieve + scan, fused)",
+                     "ops_per_odd_n": ops_per_n, "kernel_avg_ms": tile_avg_s * 1e3,
+                     "kernel_share": tile_ms / total_ms if total_ms else None,
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 INT32 lanes x {sm_max:.0f} MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(e2e_steps, 1),
+                "d2h_bytes_per_step": d2h // max(e2e_steps, 1)},
+        "gpu_launches": launches,
+        "kernels": {"tile_ms_per_step": tile_ms / max(tile_n, 1),
+                    "bucket_fill_ms_per_step": bucket_ms / max(bucket_n, 1) if bucket_n else 0.0},
+        "clocks": clk,
+        "result": {"hist": res.hist[1:16], "kmax": res.kmax, "failures": res.fail_len,
+                   "list_len": res.list_len},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(lo, hi, args.cpu_seconds, 1 << 34)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    v.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

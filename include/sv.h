@@ -1,0 +1,266 @@
+/*
+ * sv.h -- C ABI of the GB300 (sm_103a) squarefree + power-of-two verifier.
+ *
+ * The operation (C. Hercher, "On the Sum of Squarefree Integers and a Power of
+ * Two", arXiv 2411.01964): for every odd n > 1 find the smallest k >= 1 such
+ * that n - 2^k is a positive squarefree integer (the Conjecture in Sec. 1 and
+ * the Theorem in Sec. 4), called mink(n) below.  The library computes it with
+ * Algorithm 1 (a sieve of the odd squarefree integers, Sec. 3) followed by
+ * Algorithm 2 (the per-n search over k, Sec. 3), and aggregates the results the
+ * way Sec. 3 "Collecting the results" does (sum and maximum of k), extended to
+ * a histogram over k, first occurrences (the records of Table 3) and lists.
+ *
+ * Conventions shared by every entry point
+ *   - All arithmetic is exact unsigned 64-bit integer arithmetic; no floating
+ *     point is used anywhere on the GPU path.
+ *   - squarefree(s): s >= 1 and no prime p with p^2 | s.  1 is squarefree.
+ *   - mink(n) = min{ k >= 1 : 2^k < n and n - 2^k squarefree }.  If no such k
+ *     exists n is a "failure" (the case Algorithm 2 prints as "no
+ *     representation found"; it never occurred in the paper).
+ *   - A range [lo, hi) is half-open (Algorithm 1's "[start; end[") and covers
+ *     the odd n with max(lo, 3) <= n < hi (the Conjecture asks n > 1).
+ *   - Limits: hi <= 2^62, and the prime table set up by sv_init_primes(max_hi)
+ *     must cover the request: hi <= max_hi (else SV_ERANGE).
+ *   - Every call returns an sv_status; the library never aborts, traps or
+ *     exits the process.  Device faults are reported as SV_ECUDA.
+ *   - Ownership: the context owns all device memory it allocates; caller
+ *     buffers (host or device, as documented per call) stay owned by the caller
+ *     and are only written, never freed or retained past the call (sv_submit:
+ *     past completion).
+ *   - Threading: one context may be used from several host threads for
+ *     sv_submit / sv_poll / sv_cancel.  The blocking calls (sv_verify_range,
+ *     sv_verify_batch, sv_min_k, sv_sieve_bitmap) and the device-resident
+ *     calls are serialised per context by an internal mutex.
+ */
+#ifndef SV_H
+#define SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sv_status {
+    SV_OK = 0,
+    SV_EINVAL = 1,      /* invalid argument (NULL pointer, lo > hi, bad config) */
+    SV_ERANGE = 2,      /* hi beyond 2^62 or beyond the prime table (sv_init_primes) */
+    SV_ENOMEM = 3,      /* host or device allocation failed; admission refused */
+    SV_EAGAIN = 4,      /* sv_poll: the request has not finished yet */
+    SV_ETIMEDOUT = 5,   /* a bounded wait ran out */
+    SV_ECANCELLED = 6,  /* the request was cancelled */
+    SV_ECUDA = 7,       /* a CUDA runtime call or kernel failed */
+    SV_ENOPRIMES = 8,   /* sv_init_primes has not been called */
+    SV_ENOTFOUND = 9,   /* unknown ticket */
+    SV_EOVERFLOW = 10   /* an internal device buffer overflowed and the retry failed */
+} sv_status;
+
+typedef struct sv_ctx sv_ctx; /* opaque: prime table, scratch, streams, graphs, server */
+
+/*
+ * Tuning knobs.  Every field may be 0, meaning "choose automatically" (the
+ * built-in defaults, or the values found by sv_autotune).  None of them
+ * changes any result; they only change speed and memory.
+ */
+typedef struct sv_config {
+    uint32_t tile_log2;          /* odd numbers per shared-memory tile = 2^tile_log2 (14..20) */
+    uint32_t margin_log2;        /* look-back below each tile, in integers: W = 2^margin_log2
+                                    (6..tile_log2+1).  n - 2^k with 2^k <= W is read from the
+                                    tile's own window; larger k go to the exact straggler test */
+    uint32_t threads;            /* threads per CTA of the tile kernel (256, 512 or 1024) */
+    uint32_t large_prime_min;    /* primes p >= this are delivered through per-tile buckets */
+    uint32_t bucket_capacity;    /* entries per tile bucket (grown automatically on overflow) */
+    uint32_t record_k_threshold; /* T: every n with mink(n) >= T is listed (default 6) */
+    uint32_t ctas_per_sm;        /* resident tile CTAs per SM (1 or 2) */
+    uint32_t reserved0;
+    uint64_t list_capacity;      /* device list entries per range (grown on overflow) */
+    uint64_t device_mem_budget;  /* bytes the serving loop may hold for requests in flight */
+    void *cuda_stream;           /* cudaStream_t used for all work; NULL = a library stream */
+} sv_config;
+
+/*
+ * Result of one range, filled by sv_verify_range / sv_verify_batch / sv_poll.
+ * The caller sets the buffer pointers and capacities (any may be NULL with
+ * capacity 0) before the call; everything else is written by the library.
+ */
+typedef struct sv_range_result {
+    uint64_t lo, hi;          /* echoed */
+    uint64_t n_odd;           /* number of odd n in [max(lo,3), hi) */
+    uint64_t hist[64];        /* hist[k] = #odd n with mink(n) = k (hist[0] unused) */
+    uint64_t first_n[64];     /* smallest n with mink(n) = k; UINT64_MAX if none */
+    uint64_t ksum;            /* sum of mink over the range (Sec. 3 "Collecting the results") */
+    uint64_t kmax;            /* largest mink in the range (same section) */
+    uint64_t *list;           /* caller-owned, ascending: every n with mink(n) >= T */
+    uint8_t *list_k;          /* caller-owned: mink of list[i] (may be NULL) */
+    uint64_t list_cap;        /* capacity of list / list_k */
+    uint64_t list_len;        /* entries found; may exceed list_cap (then truncated) */
+    uint64_t *failures;       /* caller-owned, ascending: odd n without any k */
+    uint64_t fail_cap;
+    uint64_t fail_len;        /* failures found; may exceed fail_cap (then truncated) */
+    uint8_t *per_n_k;         /* optional, caller-owned HOST buffer of n_odd bytes: mink of the
+                                 i-th odd n of the range at index i; 255 = failure; NULL = skip */
+    uint64_t list_overflow;   /* 1 if list_len > list_cap */
+} sv_range_result;
+
+typedef enum sv_request_kind { SV_REQ_RANGE = 0, SV_REQ_POINTS = 1 } sv_request_kind;
+
+/* One serving request (sv_submit). Buffers must stay valid until sv_poll
+ * returns SV_OK or SV_ECANCELLED for its ticket. */
+typedef struct sv_request {
+    uint32_t kind;            /* sv_request_kind */
+    uint32_t reserved;
+    uint64_t lo, hi;          /* SV_REQ_RANGE */
+    sv_range_result *result;  /* SV_REQ_RANGE: caller-owned host result */
+    const uint64_t *points;   /* SV_REQ_POINTS: caller-owned host array */
+    uint64_t n_points;
+    uint8_t *out_k;           /* SV_REQ_POINTS: caller-owned host output, n_points bytes */
+} sv_request;
+
+/* Serving counters (sv_server_stats). Latencies in microseconds. */
+typedef struct sv_server_stats {
+    uint64_t submitted, completed, cancelled, refused;
+    uint64_t odd_n_done;      /* odd n verified by completed range requests + points */
+    uint64_t launches;        /* batched device launches issued */
+    uint64_t in_flight;       /* requests admitted and not yet completed */
+    uint64_t queued;          /* requests waiting for admission */
+    double p50_us, p99_us;    /* over completed requests since start */
+} sv_server_stats;
+
+/* Human-readable name of a status (static string, never NULL). */
+const char *sv_strerror(sv_status s);
+
+/*
+ * Create a context on the current CUDA device.  cfg may be NULL (all
+ * automatic).  On success *ctx owns a stream (unless cfg->cuda_stream is set)
+ * and no prime table yet.  Errors: SV_EINVAL, SV_ENOMEM, SV_ECUDA.
+ */
+sv_status sv_create(sv_ctx **ctx, const sv_config *cfg);
+
+/* Stop the server (pending requests complete as SV_ECANCELLED), free all
+ * device memory.  NULL is allowed. */
+void sv_destroy(sv_ctx *ctx);
+
+/* The effective configuration (after automatic choices). */
+sv_status sv_get_config(const sv_ctx *ctx, sv_config *out);
+
+/*
+ * Algorithm 1 needs every prime 3 <= p < sqrt(end) (Sec. 3).  Builds, on the
+ * device, the table of all odd primes p <= isqrt(max_hi - 1) with the
+ * constants the kernels use, and keeps it resident.  max_hi <= 2^62.  Calling
+ * it again with a larger max_hi rebuilds the table; a smaller one is a no-op.
+ * Errors: SV_EINVAL, SV_ERANGE, SV_ENOMEM, SV_ECUDA.
+ */
+sv_status sv_init_primes(sv_ctx *ctx, uint64_t max_hi);
+
+/* Number of odd primes in the resident table and the largest one. */
+sv_status sv_prime_count(const sv_ctx *ctx, uint64_t *count, uint64_t *largest);
+
+/*
+ * Verify one range (Algorithms 1 and 2, Sec. 3): mink of every odd n in
+ * [max(lo,3), hi), aggregated into *out.  Blocking.  out's buffers are HOST
+ * memory owned by the caller.  lo >= hi gives an empty result.
+ * Errors: SV_EINVAL, SV_ERANGE, SV_ENOPRIMES, SV_ENOMEM, SV_ECUDA, SV_EOVERFLOW.
+ */
+sv_status sv_verify_range(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_range_result *out);
+
+/*
+ * Verify `count` independent ranges [lo[i], hi[i]) in one batched, persistent,
+ * CUDA-graph launch (all tiles of all ranges share one work queue).  out[i]
+ * as for sv_verify_range.  Blocking.
+ */
+sv_status sv_verify_batch(sv_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t count,
+                          sv_range_result *out);
+
+/*
+ * mink of single points (Algorithm 2 for one n, with every n - 2^k decided by
+ * an exact squarefree test).  points and out_k are HOST arrays of `count`
+ * entries.  out_k[i] = mink(points[i]); 0 if points[i] is even or < 3; 255 if
+ * no k with 2^k < n works.  Every point must be < the table's max_hi.
+ * Errors: SV_EINVAL, SV_ERANGE, SV_ENOPRIMES, SV_ENOMEM, SV_ECUDA.
+ */
+sv_status sv_min_k(sv_ctx *ctx, const uint64_t *points, size_t count, uint8_t *out_k);
+
+/*
+ * Algorithm 1 alone: the squarefree flags of the odd integers of [lo, hi)
+ * into d_bitmap, a DEVICE buffer of sv_bitmap_words(lo, hi) uint32 words.
+ * Bit b of word i describes the odd integer m = 64*(floor(lo/64) + i) + 2b + 1
+ * (1 = squarefree); bits for m outside [lo, hi) are 0.  Blocking.
+ */
+sv_status sv_sieve_bitmap(sv_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *d_bitmap);
+uint64_t sv_bitmap_words(uint64_t lo, uint64_t hi);
+
+/*
+ * Device-resident form of sv_verify_range: enqueue the whole range on the
+ * context's stream and return without waiting; results stay in device memory
+ * until sv_fetch_range.  d_per_n_k is an optional caller-owned DEVICE buffer
+ * of n_odd bytes (NULL = skip).  One range may be pending per context.
+ */
+sv_status sv_launch_range(sv_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *d_per_n_k);
+
+/* Wait for the pending sv_launch_range and copy its aggregates to *out
+ * (out->per_n_k is ignored: the per-n values are already in the device
+ * buffer given to sv_launch_range). */
+sv_status sv_fetch_range(sv_ctx *ctx, sv_range_result *out);
+
+/* Device-resident form of sv_min_k: d_points / d_out_k are DEVICE arrays;
+ * enqueued on the context's stream, no wait. */
+sv_status sv_min_k_device(sv_ctx *ctx, const uint64_t *d_points, size_t count, uint8_t *d_out_k);
+
+/* Wait until all work enqueued on the context's stream has finished. */
+sv_status sv_synchronize(sv_ctx *ctx);
+
+/*
+ * Autotuner: times candidate tile sizes, thread counts, look-back margins and
+ * large-prime thresholds on [lo, hi) (a sample of the target workload) and
+ * keeps the fastest in the context.  Never changes results.
+ */
+sv_status sv_autotune(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_config *chosen);
+
+/*
+ * Serving.  sv_submit admits a range or point request into the request loop
+ * (continuous batching: requests that arrive while others are on the GPU are
+ * packed into the next launches as device memory and launch slots free up;
+ * long ranges are split so that they do not block short ones).  *ticket
+ * identifies it.  SV_ENOMEM: the request alone exceeds the memory budget.
+ */
+sv_status sv_submit(sv_ctx *ctx, const sv_request *req, uint64_t *ticket);
+
+/* SV_OK when the request has finished (its result is written), SV_EAGAIN if
+ * still pending after timeout_us microseconds (0 = do not wait, < 0 = wait
+ * without limit), SV_ECANCELLED, SV_ENOTFOUND.  A finished ticket is
+ * released by the call that reports it. */
+sv_status sv_poll(sv_ctx *ctx, uint64_t ticket, int64_t timeout_us);
+
+/* Cancel a request that has not started on the device yet (a running one
+ * completes normally).  SV_OK if cancelled, SV_EAGAIN if already running. */
+sv_status sv_cancel(sv_ctx *ctx, uint64_t ticket);
+
+/* Serving counters since the server started (first sv_submit). */
+sv_status sv_server_stats_get(sv_ctx *ctx, sv_server_stats *out);
+
+/* Replace the tuning knobs (same rules as sv_create; the stream is kept). */
+sv_status sv_set_config(sv_ctx *ctx, const sv_config *cfg);
+
+/* Bytes the last blocking call copied host->device and device->host
+ * (inputs, descriptors, aggregates, lists, per-n values). */
+sv_status sv_last_transfer(const sv_ctx *ctx, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
+
+/* Number of kernels this context has launched so far. */
+uint64_t sv_kernel_launches(const sv_ctx *ctx);
+
+/* Per-kernel timing: when enabled, every kernel launch is bracketed by CUDA
+ * events recorded on the stream it is launched on.  enable != 0 turns it on,
+ * 0 off; both reset the totals.  Kernel ids: 0 init, 1 bucket fill, 2 tile
+ * (sieve + scan), 3 stragglers, 4 points. */
+sv_status sv_kernel_timing(sv_ctx *ctx, int enable);
+
+/* Total milliseconds and launch count of one kernel id since the last reset
+ * (waits for the context's stream). */
+sv_status sv_kernel_time(sv_ctx *ctx, int kernel, double *total_ms, uint64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SV_H */

@@ -1,0 +1,956 @@
+// api.cu -- host runtime behind include/sv.h: context, prime table, launch
+// planning (ranges -> tiles -> buckets), the fixed kernel sequence of one
+// launch, result collection and the retry-on-overflow policy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace sv;
+
+namespace sv {
+
+void Workspace::release_all() {
+  reqs.release();
+  h_reqs.release();
+  hdr.release();
+  h_hdr.release();
+  slots.release();
+  h_slots.release();
+  list_n.release();
+  list_k.release();
+  h_list_n.release();
+  h_list_k.release();
+  fail_n.release();
+  h_fail_n.release();
+  strag.release();
+  bucket_count.release();
+  bucket_data.release();
+  per_n.release();
+  points.release();
+  points_out.release();
+  h_points.release();
+  h_points_out.release();
+}
+
+uint64_t host_isqrt(uint64_t x) {
+  // floor(sqrt(x)) by Newton's iteration from above (integer only)
+  if (x < 2) return x;
+  uint64_t r = x, y = x / 2 + 1;
+  while (y < r) {
+    r = y;
+    y = (r + x / r) / 2;
+  }
+  return r;
+}
+
+uint64_t range_odd_count(uint64_t lo, uint64_t hi) {
+  const uint64_t nlo = (lo < 3 ? 3 : lo) | 1ull;
+  return hi > nlo ? (hi - nlo + 1) / 2 : 0;
+}
+
+}  // namespace sv
+
+namespace {
+
+constexpr uint64_t kMaxHi = 1ull << 62;
+
+sv_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SV_OK : SV_ECUDA; }
+
+#define SV_TRY_CUDA(expr)                       \
+  do {                                          \
+    cudaError_t e__ = (expr);                   \
+    if (e__ != cudaSuccess) return SV_ECUDA;    \
+  } while (0)
+
+uint32_t ilog2_u32(uint32_t x) { return 31u - (uint32_t)__builtin_clz(x); }
+
+// Number of table primes p with p <= x.
+uint32_t primes_upto(const sv_ctx *c, uint64_t x) {
+  if (x > 0xFFFFFFFFull) x = 0xFFFFFFFFull;
+  return (uint32_t)(std::upper_bound(c->h_p.begin(), c->h_p.end(), (uint32_t)x) - c->h_p.begin());
+}
+
+// Defaults and validation of the tuning knobs.
+sv_status normalise_config(sv_ctx *c, sv_config *k) {
+  if (k->tile_log2 == 0) k->tile_log2 = 20;
+  if (k->margin_log2 == 0) k->margin_log2 = 16;
+  if (k->threads == 0) k->threads = 1024;
+  if (k->record_k_threshold == 0) k->record_k_threshold = 6;
+  if (k->ctas_per_sm == 0) k->ctas_per_sm = 1;
+  if (k->list_capacity == 0) k->list_capacity = 1ull << 16;
+  if (k->device_mem_budget == 0) k->device_mem_budget = 8ull << 30;
+  if (k->tile_log2 < 12 || k->tile_log2 > 20) return SV_EINVAL;
+  if (k->margin_log2 < 6 || k->margin_log2 > k->tile_log2 + 1) return SV_EINVAL;
+  if (k->threads < 128 || k->threads > 1024 || (k->threads & 31)) return SV_EINVAL;
+  if (k->record_k_threshold > 63) return SV_EINVAL;
+  if (k->ctas_per_sm > 4) return SV_EINVAL;
+  const size_t tw = 1ull << (k->tile_log2 - 5), mw = 1ull << (k->margin_log2 - 6);
+  const size_t smem = 4 * (tw + mw);
+  if (c->smem_optin && smem + 4096 > c->smem_optin) return SV_EINVAL;  // window + static data per CTA
+  if (k->large_prime_min == 0) k->large_prime_min = 1u << ((k->tile_log2 + 1) / 2);
+  return SV_OK;
+}
+
+// Largest window span (bits) of any range of a launch.
+uint64_t max_span_bits(const sv_ctx *c, const std::vector<RangeSpec> &specs) {
+  uint64_t m = 0;
+  for (const RangeSpec &s : specs)
+    if (s.hi > s.lo) m = std::max<uint64_t>(m, (s.hi - s.lo) / 2 + (1ull << c->cfg.margin_log2) / 2 + 64);
+  return m;
+}
+
+// span_bits > 0: primes are bucketed only if they hit any window of the launch
+// at most ~64 times, so that the bucket fill stays balanced (one thread walks
+// one prime's hits); smaller primes are struck per tile instead.
+Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
+  const sv_config &k = c->cfg;
+  Geometry g{};
+  g.tw = 1u << (k.tile_log2 - 5);
+  g.tw_log2 = ilog2_u32(g.tw);
+  g.mw = 1u << (k.margin_log2 - 6);
+  g.kwin = k.margin_log2;
+  g.rec_t = k.record_k_threshold;
+  g.i_med = (uint32_t)kStampCount;
+  // dense: at least 32 strikes in a full window of 32*(tw+mw) bits
+  const uint64_t dense_q = (uint64_t)g.tw + g.mw;
+  uint32_t i = g.i_med;
+  while (i < c->n_primes && (uint64_t)c->h_p[i] * c->h_p[i] <= dense_q) ++i;
+  g.i_dense = i;
+  uint64_t lp = k.large_prime_min;
+  if (span_bits) lp = std::max<uint64_t>(lp, host_isqrt(span_bits / 64) + 1);
+  uint32_t il = primes_upto(c, lp - 1);
+  if (il < g.i_dense) il = g.i_dense;
+  g.i_large = il;
+  // expected bucket hits per full window: 32*(tw+mw) * sum_{large p} 1/p^2
+  // (only sizes a buffer; overflow is detected and the launch repeated)
+  double s = 0.0;
+  for (uint32_t j = il; j < c->n_primes; ++j) s += 1.0 / ((double)c->h_p[j] * (double)c->h_p[j]);
+  const double lam = 32.0 * (double)(g.tw + g.mw) * s;
+  uint32_t cap = (uint32_t)(lam + 8.0 * std::sqrt(lam) + 64.0);
+  cap = (cap + 31u) & ~31u;
+  g.bucket_auto = cap;
+  if (k.bucket_capacity) cap = k.bucket_capacity;  // explicit override (grown on overflow)
+  g.bucket_cap = cap;
+  return g;
+}
+
+PrimeTab prime_tab(const sv_ctx *c) {
+  PrimeTab pt{};
+  pt.p = c->d_p;
+  pt.mu = c->d_mu;
+  pt.inv = c->d_inv;
+  pt.lim = c->d_lim;
+  pt.n = c->n_primes;
+  pt.n_div = c->n_div;
+  return pt;
+}
+
+sv_status ensure_tile_smem(sv_ctx *c) {
+  const size_t smem = 4ull * ((1ull << (c->cfg.tile_log2 - 5)) + (1ull << (c->cfg.margin_log2 - 6)));
+  if (smem > c->smem_set.load()) {
+    SV_TRY_CUDA(tile_kernel_setup(smem));
+    c->smem_set.store(smem);
+  }
+  return SV_OK;
+}
+
+// Plans the descriptors of `specs` into ws.h_reqs / ws.h_hdr.
+sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g, Workspace &ws) {
+  const uint32_t n = (uint32_t)specs.size();
+  if (ws.h_reqs.ensure(n ? n : 1) != cudaSuccess) return SV_ENOMEM;
+  if (ws.h_hdr.ensure(1) != cudaSuccess) return SV_ENOMEM;
+  uint64_t tiles = 0, list_total = 0, fail_total = 0;
+  uint32_t max_primes = 0;
+  bool any_per_n = false;
+  for (uint32_t r = 0; r < n; ++r) {
+    const RangeSpec &s = specs[r];
+    ReqDesc d{};
+    d.lo = s.lo;
+    d.hi = s.hi;
+    d.slot = r;
+    if (s.sieve_only) {
+      d.nlo = s.lo | 1ull;
+      d.jlo = s.lo / 2;
+    } else {
+      d.nlo = (s.lo < 3 ? 3 : s.lo) | 1ull;
+      d.jlo = (d.nlo - 1) / 2;
+    }
+    d.jhi = s.hi / 2;
+    if (d.jhi < d.jlo) d.jhi = d.jlo;
+    d.w0 = (int64_t)(d.jlo >> 5);
+    d.wend = (int64_t)((d.jhi + 31) >> 5);
+    const uint64_t nwords = (d.jhi > d.jlo) ? (uint64_t)(d.wend - d.w0) : 0;
+    const uint64_t nt = (nwords + g.tw - 1) / g.tw;
+    if (tiles + nt > 0xFFFFFFF0ull) return SV_ERANGE;
+    d.n_tiles = (uint32_t)nt;
+    d.tile_base = (uint32_t)tiles;
+    tiles += nt;
+    d.n_primes = (s.hi > 1) ? primes_upto(c, host_isqrt(s.hi - 1)) : 0;
+    if (nt && d.n_primes > max_primes) max_primes = d.n_primes;
+    d.per_n_k = s.d_per_n;
+    any_per_n |= (s.d_per_n != nullptr);
+    d.list_off = list_total;
+    d.list_cap = s.list_cap;
+    list_total += s.list_cap;
+    d.fail_off = fail_total;
+    d.fail_cap = s.fail_cap;
+    fail_total += s.fail_cap;
+    d.sieve_only = s.sieve_only ? 1u : 0u;
+    d.bitmap_out = s.bitmap_out;
+    ws.h_reqs.p[r] = d;
+  }
+  LaunchHeader h{};
+  h.n_reqs = n;
+  h.total_tiles = (uint32_t)tiles;
+  h.max_primes = max_primes;
+  *ws.h_hdr.p = h;
+  ws.n_reqs = n;
+  ws.total_tiles = (uint32_t)tiles;
+  ws.max_primes = max_primes;
+  ws.list_total = list_total;
+  ws.fail_total = fail_total;
+  ws.any_per_n = any_per_n;
+  return SV_OK;
+}
+
+// Kernel ids of the per-kernel timing.
+enum { kKInit = 0, kKBucket = 1, kKTiles = 2, kKStrag = 3, kKPoints = 4 };
+
+cudaEvent_t pool_event(sv_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with events when timing is enabled.
+struct KTimer {
+  sv_ctx *c;
+  int id;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  KTimer(sv_ctx *c_, int id_, cudaStream_t st_) : c(c_), id(id_), st(st_) {
+    if (c->kprof && st == c->stream) {  // the serving thread's streams are never timed
+      a = pool_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  void done() {
+    if (a) {
+      cudaEvent_t b = pool_event(c);
+      cudaEventRecord(b, st);
+      c->kev.push_back({id, a, b});
+    }
+  }
+};
+
+// Enqueues init -> bucket fill -> tiles -> stragglers for the planned launch.
+sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) {
+  const uint32_t n = ws.n_reqs;
+  if (ws.reqs.ensure(n ? n : 1) || ws.hdr.ensure(1) || ws.slots.ensure(n ? n : 1) ||
+      ws.h_slots.ensure(n ? n : 1) || ws.list_n.ensure(ws.list_total ? ws.list_total : 1) ||
+      ws.list_k.ensure(ws.list_total ? ws.list_total : 1) || ws.fail_n.ensure(ws.fail_total ? ws.fail_total : 1) ||
+      ws.strag.ensure(ws.strag_cap) || ws.bucket_count.ensure(ws.total_tiles ? ws.total_tiles : 1) ||
+      ws.bucket_data.ensure((size_t)(ws.total_tiles ? ws.total_tiles : 1) * g.bucket_cap))
+    return SV_ENOMEM;
+  ws.bucket_cap = g.bucket_cap;
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, st));
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.hdr.p, ws.h_hdr.p, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st));
+  ws.h2d_bytes = sizeof(ReqDesc) * n + sizeof(LaunchHeader);
+  {
+    KTimer kt(c, kKInit, st);
+    SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, ws.total_tiles, st));
+    kt.done();
+  }
+  c->launches++;
+  const PrimeTab pt = prime_tab(c);
+  if (ws.max_primes > g.i_large && ws.total_tiles) {
+    BucketArgs b{};
+    b.pt = pt;
+    b.g = g;
+    b.reqs = ws.reqs.p;
+    b.hdr = ws.hdr.p;
+    b.bucket_count = ws.bucket_count.p;
+    b.bucket_data = ws.bucket_data.p;
+    KTimer kt(c, kKBucket, st);
+    SV_TRY_CUDA(launch_bucket_fill(b, ws.max_primes - g.i_large, n, st));
+    kt.done();
+    c->launches++;
+  }
+  if (ws.total_tiles) {
+    TileArgs t{};
+    t.pt = pt;
+    t.g = g;
+    t.reqs = ws.reqs.p;
+    t.hdr = ws.hdr.p;
+    t.slots = ws.slots.p;
+    t.list_n = ws.list_n.p;
+    t.list_k = ws.list_k.p;
+    t.fail_n = ws.fail_n.p;
+    t.strag = ws.strag.p;
+    t.strag_cap = ws.strag_cap;
+    t.bucket_count = ws.bucket_count.p;
+    t.bucket_data = ws.bucket_data.p;
+    const size_t smem = 4ull * (g.tw + g.mw);
+    uint32_t grid = (uint32_t)c->num_sms * c->cfg.ctas_per_sm;
+    if (grid > ws.total_tiles) grid = ws.total_tiles;
+    {
+      KTimer kt(c, kKTiles, st);
+      SV_TRY_CUDA(launch_tiles(t, c->cfg.threads, grid, smem, ws.any_per_n, st));
+      kt.done();
+    }
+    c->launches++;
+    StragArgs s{};
+    s.pt = pt;
+    s.reqs = ws.reqs.p;
+    s.hdr = ws.hdr.p;
+    s.slots = ws.slots.p;
+    s.list_n = ws.list_n.p;
+    s.list_k = ws.list_k.p;
+    s.fail_n = ws.fail_n.p;
+    s.strag = ws.strag.p;
+    s.strag_cap = ws.strag_cap;
+    s.rec_t = g.rec_t;
+    {
+      KTimer kt(c, kKStrag, st);
+      SV_TRY_CUDA(launch_stragglers(s, (uint32_t)c->num_sms * 2, st));
+      kt.done();
+    }
+    c->launches++;
+  }
+  return SV_OK;
+}
+
+enum Collect { kDone, kRetryBucket, kRetryStrag, kRetryList };
+constexpr uint64_t kListRetryMax = 1ull << 26;  // larger lists are returned truncated, unordered
+
+// Waits for the launch, checks the device status word and copies results out.
+sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_result **outs, Workspace &ws,
+                  cudaStream_t st, Collect *what) {
+  const uint32_t n = ws.n_reqs;
+  *what = kDone;
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.h_hdr.p, ws.hdr.p, sizeof(LaunchHeader), cudaMemcpyDeviceToHost, st));
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.h_slots.p, ws.slots.p, sizeof(ResultSlot) * n, cudaMemcpyDeviceToHost, st));
+  SV_TRY_CUDA(cudaStreamSynchronize(st));
+  uint64_t d2h = sizeof(LaunchHeader) + sizeof(ResultSlot) * n;
+  const uint32_t status = ws.h_hdr.p->status;
+  if (status & kStBadTile) return SV_ECUDA;
+  if (status & kStBucketOverflow) {
+    *what = kRetryBucket;
+    return SV_OK;
+  }
+  if (status & kStStragOverflow) {
+    *what = kRetryStrag;
+    return SV_OK;
+  }
+  // lists that the device truncated must be re-run with exact room, so that
+  // the caller receives the smallest entries, deterministically
+  for (uint32_t r = 0; r < n; ++r) {
+    const ResultSlot &s = ws.h_slots.p[r];
+    if (outs && outs[r] && outs[r]->list_cap && s.list_count > specs[r].list_cap &&
+        specs[r].list_cap < kListRetryMax) {
+      *what = kRetryList;
+      return SV_OK;
+    }
+  }
+  for (uint32_t r = 0; r < n; ++r) {
+    if (!outs || !outs[r]) continue;
+    sv_range_result *o = outs[r];
+    const ResultSlot &s = ws.h_slots.p[r];
+    const RangeSpec &sp = specs[r];
+    o->lo = sp.lo;
+    o->hi = sp.hi;
+    o->n_odd = range_odd_count(sp.lo, sp.hi);
+    o->ksum = 0;
+    o->kmax = 0;
+    for (int k = 0; k < kMaxK; ++k) {
+      o->hist[k] = s.hist[k];
+      o->first_n[k] = s.first_n[k];
+      if (k > 0) {
+        o->ksum += (uint64_t)k * s.hist[k];
+        if (s.hist[k]) o->kmax = (uint64_t)k;
+      }
+    }
+    o->list_len = s.list_count;
+    o->fail_len = s.fail_count;
+    o->list_overflow = s.list_count > o->list_cap ? 1 : 0;
+    const ReqDesc &d = ws.h_reqs.p[r];
+    const uint64_t nl = std::min<uint64_t>(s.list_count, d.list_cap);
+    if (nl && (o->list || o->list_k)) {
+      if (ws.h_list_n.ensure(nl) || ws.h_list_k.ensure(nl)) return SV_ENOMEM;
+      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_n.p, ws.list_n.p + d.list_off, 8 * nl, cudaMemcpyDeviceToHost, st));
+      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_k.p, ws.list_k.p + d.list_off, nl, cudaMemcpyDeviceToHost, st));
+      SV_TRY_CUDA(cudaStreamSynchronize(st));
+      d2h += 9 * nl;
+      std::vector<std::pair<uint64_t, uint8_t>> v(nl);
+      for (uint64_t i = 0; i < nl; ++i) v[i] = {ws.h_list_n.p[i], ws.h_list_k.p[i]};
+      std::sort(v.begin(), v.end());
+      const uint64_t m = std::min<uint64_t>(nl, o->list_cap);
+      for (uint64_t i = 0; i < m; ++i) {
+        if (o->list) o->list[i] = v[i].first;
+        if (o->list_k) o->list_k[i] = v[i].second;
+      }
+    }
+    const uint64_t nf = std::min<uint64_t>(s.fail_count, d.fail_cap);
+    if (nf && o->failures) {
+      if (ws.h_fail_n.ensure(nf)) return SV_ENOMEM;
+      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_fail_n.p, ws.fail_n.p + d.fail_off, 8 * nf, cudaMemcpyDeviceToHost, st));
+      SV_TRY_CUDA(cudaStreamSynchronize(st));
+      d2h += 8 * nf;
+      std::sort(ws.h_fail_n.p, ws.h_fail_n.p + nf);
+      const uint64_t m = std::min<uint64_t>(nf, o->fail_cap);
+      std::memcpy(o->failures, ws.h_fail_n.p, 8 * m);
+    }
+  }
+  ws.d2h_bytes = d2h;
+  return SV_OK;
+}
+
+sv_status check_ready(sv_ctx *c) {
+  if (!c) return SV_EINVAL;
+  if (!c->d_p) return SV_ENOPRIMES;
+  return SV_OK;
+}
+
+sv_status check_range(const sv_ctx *c, uint64_t lo, uint64_t hi) {
+  (void)lo;
+  if (hi > kMaxHi) return SV_ERANGE;
+  if (hi > c->max_hi) return SV_ERANGE;
+  return SV_OK;
+}
+
+}  // namespace
+
+namespace sv {
+
+// Runs a launch of ranges to completion, growing buffers and repeating the
+// launch when the device reports an overflow.  Results never depend on the
+// buffer sizes.
+sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result **outs, cudaStream_t st,
+                     Workspace &ws) {
+  sv_status s = ensure_tile_smem(c);
+  if (s) return s;
+  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  if (ws.bucket_cap > g.bucket_cap) g.bucket_cap = ws.bucket_cap;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    if ((s = plan(c, specs, g, ws))) return s;
+    if ((s = enqueue(c, g, ws, st))) return s;
+    Collect what;
+    if ((s = collect(c, specs, outs, ws, st, &what))) return s;
+    if (what == kDone) {
+      c->last_h2d = ws.h2d_bytes;
+      c->last_d2h = ws.d2h_bytes;
+      return SV_OK;
+    }
+    if (what == kRetryBucket) {
+      g.bucket_cap = std::max<uint32_t>(g.bucket_cap * 4, g.bucket_auto);
+      ws.bucket_cap = g.bucket_cap;
+    }
+    if (what == kRetryStrag) ws.strag_cap *= 4;
+    if (what == kRetryList) {
+      for (uint32_t r = 0; r < specs.size(); ++r) {
+        const uint64_t cnt = ws.h_slots.p[r].list_count;
+        if (outs && outs[r] && cnt > specs[r].list_cap) specs[r].list_cap = std::min<uint64_t>(cnt, kListRetryMax);
+      }
+    }
+  }
+  return SV_EOVERFLOW;
+}
+
+sv_status launch_ranges_async(sv_ctx *c, std::vector<RangeSpec> &specs, Workspace &ws, cudaStream_t st) {
+  sv_status s = ensure_tile_smem(c);
+  if (s) return s;
+  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  if (ws.bucket_cap > g.bucket_cap) g.bucket_cap = ws.bucket_cap;
+  if ((s = plan(c, specs, g, ws))) return s;
+  return enqueue(c, g, ws, st);
+}
+
+sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_result **outs, Workspace &ws,
+                         cudaStream_t st, bool *retry) {
+  Collect what;
+  sv_status s = collect(c, specs, outs, ws, st, &what);
+  *retry = (what != kDone);
+  if (what == kRetryBucket)
+    ws.bucket_cap = std::max<uint32_t>(ws.bucket_cap * 4, make_geometry(c, max_span_bits(c, specs)).bucket_auto);
+  if (what == kRetryStrag) ws.strag_cap *= 4;
+  return s;
+}
+
+sv_status launch_points_async(sv_ctx *c, uint64_t count, Workspace &ws, cudaStream_t st) {
+  if (count == 0) return SV_OK;
+  if (ws.points.ensure(count) || ws.points_out.ensure(count)) return SV_ENOMEM;
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.points.p, ws.h_points.p, 8 * count, cudaMemcpyHostToDevice, st));
+  uint64_t grid = (count * 32 + 255) / 256;
+  const uint64_t gmax = (uint64_t)c->num_sms * 8;
+  if (grid > gmax) grid = gmax;
+  SV_TRY_CUDA(launch_points(prime_tab(c), ws.points.p, count, ws.points_out.p, (uint32_t)grid, st));
+  c->launches++;
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.h_points_out.p, ws.points_out.p, count, cudaMemcpyDeviceToHost, st));
+  return SV_OK;
+}
+
+sv_status run_points(sv_ctx *c, const uint64_t *points, size_t count, uint8_t *out_k, cudaStream_t st,
+                     Workspace &ws) {
+  if (count == 0) return SV_OK;
+  for (size_t i = 0; i < count; ++i)
+    if (points[i] > c->max_hi) return SV_ERANGE;
+  if (ws.points.ensure(count) || ws.points_out.ensure(count) || ws.h_points.ensure(count) ||
+      ws.h_points_out.ensure(count))
+    return SV_ENOMEM;
+  std::memcpy(ws.h_points.p, points, 8 * count);
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.points.p, ws.h_points.p, 8 * count, cudaMemcpyHostToDevice, st));
+  uint64_t warps = count;
+  uint64_t grid = (warps * 32 + 255) / 256;
+  const uint64_t gmax = (uint64_t)c->num_sms * 8;
+  if (grid > gmax) grid = gmax;
+  {
+    KTimer kt(c, kKPoints, st);
+    SV_TRY_CUDA(launch_points(prime_tab(c), ws.points.p, count, ws.points_out.p, (uint32_t)grid, st));
+    kt.done();
+  }
+  c->launches++;
+  SV_TRY_CUDA(cudaMemcpyAsync(ws.h_points_out.p, ws.points_out.p, count, cudaMemcpyDeviceToHost, st));
+  SV_TRY_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(out_k, ws.h_points_out.p, count);
+  c->last_h2d = 8 * count;
+  c->last_d2h = count;
+  return SV_OK;
+}
+
+}  // namespace sv
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *sv_strerror(sv_status s) {
+  switch (s) {
+    case SV_OK: return "ok";
+    case SV_EINVAL: return "invalid argument";
+    case SV_ERANGE: return "out of range (hi beyond 2^62 or beyond the prime table)";
+    case SV_ENOMEM: return "out of memory / admission refused";
+    case SV_EAGAIN: return "not finished yet";
+    case SV_ETIMEDOUT: return "timed out";
+    case SV_ECANCELLED: return "cancelled";
+    case SV_ECUDA: return "CUDA error";
+    case SV_ENOPRIMES: return "prime table not initialised (sv_init_primes)";
+    case SV_ENOTFOUND: return "unknown ticket";
+    case SV_EOVERFLOW: return "device buffer overflow persisted after retries";
+  }
+  return "unknown status";
+}
+
+sv_status sv_create(sv_ctx **out, const sv_config *cfg) {
+  if (!out) return SV_EINVAL;
+  *out = nullptr;
+  sv_ctx *c = new (std::nothrow) sv_ctx();
+  if (!c) return SV_ENOMEM;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return SV_ECUDA;
+  }
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device) != cudaSuccess) {
+    delete c;
+    return SV_ECUDA;
+  }
+  c->smem_optin = (size_t)optin;
+  if (cfg) c->cfg = *cfg;
+  sv_status s = normalise_config(c, &c->cfg);
+  if (s) {
+    delete c;
+    return s;
+  }
+  if (c->cfg.cuda_stream) {
+    c->stream = (cudaStream_t)c->cfg.cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return SV_ECUDA;
+    }
+    c->own_stream = true;
+    c->cfg.cuda_stream = c->stream;
+  }
+  *out = c;
+  return SV_OK;
+}
+
+void sv_destroy(sv_ctx *c) {
+  if (!c) return;
+  if (c->server) server_destroy(c->server);
+  c->server = nullptr;
+  cudaStreamSynchronize(c->stream);
+  c->ws.release_all();
+  cudaFree(c->d_p);
+  cudaFree(c->d_mu);
+  cudaFree(c->d_inv);
+  cudaFree(c->d_lim);
+  for (auto &k : c->kev) {
+    cudaEventDestroy(k.a);
+    cudaEventDestroy(k.b);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+sv_status sv_get_config(const sv_ctx *c, sv_config *out) {
+  if (!c || !out) return SV_EINVAL;
+  *out = c->cfg;
+  return SV_OK;
+}
+
+sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
+  if (!c) return SV_EINVAL;
+  if (max_hi > kMaxHi) return SV_ERANGE;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (c->d_p && max_hi <= c->max_hi) return SV_OK;
+  const uint64_t pmax = host_isqrt(max_hi > 1 ? max_hi - 1 : 1);
+  uint32_t *d_p = nullptr;
+  uint64_t *d_mu = nullptr, *d_inv = nullptr, *d_lim = nullptr;
+  uint32_t n = 0, n_div = 0;
+  cudaError_t e = build_prime_table(pmax, &d_p, &d_mu, &d_inv, &d_lim, &n, &n_div, c->stream);
+  if (e == cudaErrorMemoryAllocation) return SV_ENOMEM;
+  if (e != cudaSuccess) return SV_ECUDA;
+  std::vector<uint32_t> hp(n);
+  if (n && cudaMemcpy(hp.data(), d_p, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaFree(d_p);
+    cudaFree(d_mu);
+    cudaFree(d_inv);
+    cudaFree(d_lim);
+    return SV_ECUDA;
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->d_p);
+  cudaFree(c->d_mu);
+  cudaFree(c->d_inv);
+  cudaFree(c->d_lim);
+  c->d_p = d_p;
+  c->d_mu = d_mu;
+  c->d_inv = d_inv;
+  c->d_lim = d_lim;
+  c->n_primes = n;
+  c->n_div = n_div;
+  c->h_p.swap(hp);
+  c->pmax = pmax;
+  c->max_hi = max_hi;
+  c->launches += 5;
+  return SV_OK;
+}
+
+sv_status sv_prime_count(const sv_ctx *c, uint64_t *count, uint64_t *largest) {
+  if (!c) return SV_EINVAL;
+  if (count) *count = c->n_primes;
+  if (largest) *largest = c->n_primes ? c->h_p.back() : 0;
+  return SV_OK;
+}
+
+uint64_t sv_bitmap_words(uint64_t lo, uint64_t hi) {
+  const uint64_t jlo = lo / 2, jhi = hi / 2;
+  if (jhi <= jlo) return 0;
+  return ((jhi + 31) >> 5) - (jlo >> 5);
+}
+
+sv_status sv_verify_range(sv_ctx *c, uint64_t lo, uint64_t hi, sv_range_result *out) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (!out) return SV_EINVAL;
+  if ((s = check_range(c, lo, hi))) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<RangeSpec> specs(1);
+  specs[0].lo = lo;
+  specs[0].hi = hi;
+  specs[0].list_cap = out->list_cap;
+  specs[0].fail_cap = std::max<uint64_t>(out->fail_cap, 64);
+  const uint64_t n_odd = range_odd_count(lo, hi);
+  if (out->per_n_k && n_odd) {
+    if (c->ws.per_n.ensure(n_odd)) return SV_ENOMEM;
+    specs[0].d_per_n = c->ws.per_n.p;
+  }
+  sv_range_result *outs[1] = {out};
+  s = run_ranges(c, specs, outs, c->stream, c->ws);
+  if (s) return s;
+  if (out->per_n_k && n_odd) {
+    if (cudaMemcpyAsync(out->per_n_k, c->ws.per_n.p, n_odd, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return SV_ECUDA;
+    c->last_d2h += n_odd;
+  }
+  return SV_OK;
+}
+
+sv_status sv_verify_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t count, sv_range_result *out) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (count && (!lo || !hi || !out)) return SV_EINVAL;
+  for (size_t i = 0; i < count; ++i)
+    if ((s = check_range(c, lo[i], hi[i]))) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<RangeSpec> specs(count);
+  std::vector<sv_range_result *> outs(count);
+  for (size_t i = 0; i < count; ++i) {
+    specs[i].lo = lo[i];
+    specs[i].hi = hi[i];
+    specs[i].list_cap = out[i].list_cap;
+    specs[i].fail_cap = std::max<uint64_t>(out[i].fail_cap, 16);
+    outs[i] = &out[i];
+  }
+  if (count == 0) return SV_OK;
+  return run_ranges(c, specs, outs.data(), c->stream, c->ws);
+}
+
+sv_status sv_min_k(sv_ctx *c, const uint64_t *points, size_t count, uint8_t *out_k) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (count && (!points || !out_k)) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  return run_points(c, points, count, out_k, c->stream, c->ws);
+}
+
+sv_status sv_min_k_device(sv_ctx *c, const uint64_t *d_points, size_t count, uint8_t *d_out_k) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (count && (!d_points || !d_out_k)) return SV_EINVAL;
+  if (count == 0) return SV_OK;
+  std::lock_guard<std::mutex> lk(c->mu);
+  uint64_t grid = ((uint64_t)count * 32 + 255) / 256;
+  const uint64_t gmax = (uint64_t)c->num_sms * 8;
+  if (grid > gmax) grid = gmax;
+  if (launch_points(prime_tab(c), d_points, count, d_out_k, (uint32_t)grid, c->stream) != cudaSuccess)
+    return SV_ECUDA;
+  c->launches++;
+  return SV_OK;
+}
+
+sv_status sv_sieve_bitmap(sv_ctx *c, uint64_t lo, uint64_t hi, uint32_t *d_bitmap) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if ((s = check_range(c, lo, hi))) return s;
+  if (sv_bitmap_words(lo, hi) == 0) return SV_OK;
+  if (!d_bitmap) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<RangeSpec> specs(1);
+  specs[0].lo = lo;
+  specs[0].hi = hi;
+  specs[0].sieve_only = true;
+  specs[0].bitmap_out = d_bitmap;
+  return run_ranges(c, specs, nullptr, c->stream, c->ws);
+}
+
+sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_k) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if ((s = check_range(c, lo, hi))) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((s = ensure_tile_smem(c))) return s;
+  std::vector<RangeSpec> specs(1);
+  specs[0].lo = lo;
+  specs[0].hi = hi;
+  specs[0].d_per_n = d_per_n_k;
+  specs[0].list_cap = c->cfg.list_capacity;
+  specs[0].fail_cap = 1024;
+  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
+  if ((s = plan(c, specs, g, c->ws))) return s;
+  if ((s = enqueue(c, g, c->ws, c->stream))) return s;
+  c->pending = true;
+  c->pending_specs = specs;
+  return SV_OK;
+}
+
+sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
+  if (!c || !out) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->pending) return SV_EINVAL;
+  c->pending = false;
+  sv_range_result *outs[1] = {out};
+  Collect what;
+  sv_status s = collect(c, c->pending_specs, outs, c->ws, c->stream, &what);
+  if (s) return s;
+  if (what != kDone) {
+    // an overflow: repeat the range with grown buffers, blocking
+    std::vector<RangeSpec> specs = c->pending_specs;
+    if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
+    if (what == kRetryStrag) c->ws.strag_cap *= 4;
+    s = run_ranges(c, specs, outs, c->stream, c->ws);
+    if (s) return s;
+  }
+  c->last_h2d = c->ws.h2d_bytes;
+  c->last_d2h = c->ws.d2h_bytes;
+  return SV_OK;
+}
+
+sv_status sv_synchronize(sv_ctx *c) {
+  if (!c) return SV_EINVAL;
+  return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+// Bytes the last blocking call moved host->device and device->host, and the
+// number of kernels the library has launched so far.
+sv_status sv_last_transfer(const sv_ctx *c, uint64_t *h2d, uint64_t *d2h) {
+  if (!c) return SV_EINVAL;
+  if (h2d) *h2d = c->last_h2d;
+  if (d2h) *d2h = c->last_d2h;
+  return SV_OK;
+}
+
+uint64_t sv_kernel_launches(const sv_ctx *c) { return c ? c->launches.load() : 0; }
+
+sv_status sv_kernel_timing(sv_ctx *c, int enable) {
+  if (!c) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SV_ECUDA;
+  for (auto &k : c->kev) {
+    c->ev_pool.push_back(k.a);
+    c->ev_pool.push_back(k.b);
+  }
+  c->kev.clear();
+  for (int i = 0; i < 8; ++i) {
+    c->k_ms[i] = 0.0;
+    c->k_n[i] = 0;
+  }
+  c->kprof = enable != 0;
+  return SV_OK;
+}
+
+sv_status sv_kernel_time(sv_ctx *c, int kernel, double *total_ms, uint64_t *launches) {
+  if (!c || kernel < 0 || kernel >= 8) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SV_ECUDA;
+  for (auto &k : c->kev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, k.a, k.b) != cudaSuccess) return SV_ECUDA;
+    c->k_ms[k.id] += ms;
+    c->k_n[k.id] += 1;
+    c->ev_pool.push_back(k.a);
+    c->ev_pool.push_back(k.b);
+  }
+  c->kev.clear();
+  if (total_ms) *total_ms = c->k_ms[kernel];
+  if (launches) *launches = c->k_n[kernel];
+  return SV_OK;
+}
+
+sv_status sv_set_config(sv_ctx *c, const sv_config *cfg) {
+  if (!c || !cfg) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  sv_config k = *cfg;
+  k.cuda_stream = c->cfg.cuda_stream;
+  sv_status s = normalise_config(c, &k);
+  if (s) return s;
+  c->cfg = k;
+  c->ws.bucket_cap = 0;
+  return SV_OK;
+}
+
+// Times a grid of tile sizes / thread counts / CTAs per SM / margins /
+// large-prime thresholds on [lo, hi) and keeps the fastest configuration.
+sv_status sv_autotune(sv_ctx *c, uint64_t lo, uint64_t hi, sv_config *chosen) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if ((s = check_range(c, lo, hi))) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  const sv_config base = c->cfg;
+  sv_config best = base;
+  double best_t = 1e300;
+  sv_range_result res;
+  std::memset(&res, 0, sizeof(res));
+  sv_range_result *outs[1] = {&res};
+  const uint32_t tiles[] = {17, 18, 19, 20};
+  const uint32_t threads[] = {512, 1024};
+  const uint32_t ctas[] = {1, 2};
+  const uint32_t margins[] = {14, 16};
+  for (uint32_t tl : tiles)
+    for (uint32_t th : threads)
+      for (uint32_t cp : ctas)
+        for (uint32_t ml : margins)
+          for (uint32_t lp_shift = 0; lp_shift < 2; ++lp_shift) {
+            sv_config k = base;
+            k.tile_log2 = tl;
+            k.threads = th;
+            k.ctas_per_sm = cp;
+            k.margin_log2 = ml < tl + 1 ? ml : tl + 1;
+            k.large_prime_min = 1u << ((tl + 1) / 2 + lp_shift);
+            k.bucket_capacity = 0;
+            const size_t smem = 4ull * ((1ull << (tl - 5)) + (1ull << (k.margin_log2 - 6)));
+            if (cp * (smem + 4096) > c->smem_optin + 4096 || (size_t)cp * th > 2048) continue;
+            if (normalise_config(c, &k)) continue;
+            c->cfg = k;
+            c->ws.bucket_cap = 0;
+            double t = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+              std::vector<RangeSpec> specs(1);
+              specs[0].lo = lo;
+              specs[0].hi = hi;
+              specs[0].fail_cap = 16;
+              const auto t0 = std::chrono::steady_clock::now();
+              s = run_ranges(c, specs, outs, c->stream, c->ws);
+              const auto t1 = std::chrono::steady_clock::now();
+              if (s) break;
+              const double dt = std::chrono::duration<double>(t1 - t0).count();
+              if (rep > 0 && dt < t) t = dt;  // first run warms up
+            }
+            if (s) {
+              c->cfg = base;
+              return s;
+            }
+            if (t < best_t) {
+              best_t = t;
+              best = k;
+            }
+          }
+  c->cfg = best;
+  c->ws.bucket_cap = 0;
+  if (chosen) *chosen = best;
+  return SV_OK;
+}
+
+sv_status sv_submit(sv_ctx *c, const sv_request *req, uint64_t *ticket) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (!req || !ticket) return SV_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->server) c->server = server_create(c);
+    if (!c->server) return SV_ENOMEM;
+  }
+  return server_submit(c->server, req, ticket);
+}
+
+sv_status sv_poll(sv_ctx *c, uint64_t ticket, int64_t timeout_us) {
+  if (!c) return SV_EINVAL;
+  if (!c->server) return SV_ENOTFOUND;
+  return server_poll(c->server, ticket, timeout_us);
+}
+
+sv_status sv_cancel(sv_ctx *c, uint64_t ticket) {
+  if (!c) return SV_EINVAL;
+  if (!c->server) return SV_ENOTFOUND;
+  return server_cancel(c->server, ticket);
+}
+
+sv_status sv_server_stats_get(sv_ctx *c, sv_server_stats *out) {
+  if (!c || !out) return SV_EINVAL;
+  if (!c->server) {
+    std::memset(out, 0, sizeof(*out));
+    return SV_OK;
+  }
+  return server_stats(c->server, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// ctx.h -- the host-side context behind the opaque sv_ctx (host runtime only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "sv.h"
+#include "sv_internal.h"
+
+namespace sv {
+
+// Growable device / pinned-host buffer (grows geometrically, never shrinks).
+template <class T, bool PINNED>
+struct Buf {
+  T *p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    size_t c = cap ? cap : 1;
+    while (c < n) c *= 2;
+    release();
+    cudaError_t e = PINNED ? cudaMallocHost((void **)&p, c * sizeof(T)) : cudaMalloc((void **)&p, c * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cap = 0;
+      return e;
+    }
+    cap = c;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) {
+      if (PINNED) cudaFreeHost(p);
+      else cudaFree(p);
+    }
+    p = nullptr;
+    cap = 0;
+  }
+};
+template <class T> using DBuf = Buf<T, false>;
+template <class T> using HBuf = Buf<T, true>;
+
+// One range of a launch as the host plans it.
+struct RangeSpec {
+  uint64_t lo = 0, hi = 0;
+  uint8_t *d_per_n = nullptr;   // device per-n output or null
+  uint64_t list_cap = 0;        // device list entries reserved for it
+  uint64_t fail_cap = 0;
+  bool sieve_only = false;
+  uint32_t *bitmap_out = nullptr;
+};
+
+// Everything one launch needs on the device, reused across launches.
+struct Workspace {
+  DBuf<ReqDesc> reqs;
+  HBuf<ReqDesc> h_reqs;
+  DBuf<LaunchHeader> hdr;
+  HBuf<LaunchHeader> h_hdr;
+  DBuf<ResultSlot> slots;
+  HBuf<ResultSlot> h_slots;
+  DBuf<uint64_t> list_n;
+  DBuf<uint8_t> list_k;
+  HBuf<uint64_t> h_list_n;
+  HBuf<uint8_t> h_list_k;
+  DBuf<uint64_t> fail_n;
+  HBuf<uint64_t> h_fail_n;
+  DBuf<Straggler> strag;
+  DBuf<uint32_t> bucket_count;
+  DBuf<uint32_t> bucket_data;
+  DBuf<uint8_t> per_n;
+  DBuf<uint64_t> points;
+  DBuf<uint8_t> points_out;
+  HBuf<uint64_t> h_points;
+  HBuf<uint8_t> h_points_out;
+  // sizes of the launch currently described by the buffers
+  uint32_t n_reqs = 0, total_tiles = 0, max_primes = 0;
+  uint64_t list_total = 0, fail_total = 0;
+  uint32_t strag_cap = 1u << 16;
+  uint32_t bucket_cap = 0;
+  bool any_per_n = false;
+  uint64_t h2d_bytes = 0, d2h_bytes = 0;
+  void release_all();
+};
+
+class Server;  // serving loop (server.cu)
+
+}  // namespace sv
+
+struct sv_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  sv_config cfg{};          // effective configuration
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::mutex mu;            // serialises the blocking / device-resident calls
+  // prime table
+  uint64_t max_hi = 0, pmax = 0;
+  uint32_t *d_p = nullptr;
+  uint64_t *d_mu = nullptr, *d_inv = nullptr, *d_lim = nullptr;
+  uint32_t n_primes = 0, n_div = 0;
+  std::vector<uint32_t> h_p;
+  std::atomic<size_t> smem_set{0};  // dynamic smem the tile kernel was configured for
+  sv::Workspace ws;
+  // device-resident pending launch
+  bool pending = false;
+  std::vector<sv::RangeSpec> pending_specs;
+  // per-kernel timing with events on the launching stream (sv_kernel_timing)
+  bool kprof = false;
+  struct KEv {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<KEv> kev;
+  std::vector<cudaEvent_t> ev_pool;
+  double k_ms[8] = {0};
+  uint64_t k_n[8] = {0};
+  // counters
+  std::atomic<uint64_t> launches{0};
+  uint64_t last_h2d = 0, last_d2h = 0;
+  sv::Server *server = nullptr;
+};
+
+namespace sv {
+// Shared by api.cu and server.cu.
+sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result **outs, cudaStream_t st,
+                     Workspace &ws);
+sv_status run_points(sv_ctx *c, const uint64_t *points, size_t count, uint8_t *out_k, cudaStream_t st,
+                     Workspace &ws);
+// Asynchronous halves used by the serving loop: enqueue a launch of ranges on
+// `st` (no wait), then later collect it (waits for `st`); *retry is set when
+// the device reported an overflow and the launch must be repeated.
+sv_status launch_ranges_async(sv_ctx *c, std::vector<RangeSpec> &specs, Workspace &ws, cudaStream_t st);
+sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_result **outs, Workspace &ws,
+                         cudaStream_t st, bool *retry);
+// Points already staged in ws.h_points: upload, test, download into
+// ws.h_points_out (no wait).
+sv_status launch_points_async(sv_ctx *c, uint64_t count, Workspace &ws, cudaStream_t st);
+uint64_t host_isqrt(uint64_t x);
+uint64_t range_odd_count(uint64_t lo, uint64_t hi);
+Server *server_create(sv_ctx *c);
+void server_destroy(Server *s);
+sv_status server_submit(Server *s, const sv_request *req, uint64_t *ticket);
+sv_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us);
+sv_status server_cancel(Server *s, uint64_t ticket);
+sv_status server_stats(Server *s, sv_server_stats *out);
+}  // namespace sv

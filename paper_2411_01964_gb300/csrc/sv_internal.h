@@ -1,0 +1,158 @@
+// sv_internal.h -- types shared by the kernels and the host runtime of the
+// GPU library (never by the CPU oracle).
+//
+// Bit layout used everywhere on the device: bit J (J >= 0) stands for the odd
+// integer 2J + 1, word a holds bits 32a .. 32a+31 (LSB first), i.e. the odd
+// integers 64a+1 .. 64a+63.  With this layout n - 2^k (k >= 1) sits exactly
+// 2^(k-1) bits below n, which is what the word-parallel form of Algorithm 2
+// (Sec. 3) exploits: k <= 5 are funnel shifts inside a word pair, k >= 6 are
+// whole-word offsets 2^(k-6).
+#pragma once
+
+#include <cstdint>
+
+namespace sv {
+
+constexpr int kMaxK = 64;
+constexpr uint8_t kFailK = 255;
+constexpr unsigned long long kNoN = ~0ull;
+
+// Status bits raised by the kernels (ORed into a device word).
+enum : uint32_t {
+  kStBucketOverflow = 1u << 0,  // a tile bucket was full: rerun with a larger one
+  kStStragOverflow = 1u << 1,   // straggler queue full: rerun with a larger one
+  kStBadTile = 1u << 2,         // a tile index failed a bounds check
+};
+
+// Resident table of the odd primes 3 <= p <= pmax (ascending), structure of
+// arrays.  mu[i] = floor((2^64-1) / p^2) is the Barrett (1986) constant for
+// x mod p^2; inv[i] = p^-1 mod 2^64 and lim[i] = floor((2^64-1)/p) give the
+// Granlund-Montgomery (1994, Sec. 9) divisibility test  p | x  <=>
+// x * inv mod 2^64 <= lim.  inv/lim exist for the first n_div primes (all
+// p < 2^21, enough for every cube root below 2^62).
+struct PrimeTab {
+  const uint32_t *p;
+  const uint64_t *mu;
+  const uint64_t *inv;
+  const uint64_t *lim;
+  uint32_t n;
+  uint32_t n_div;
+};
+
+// One range of a launch, in device memory.
+struct ReqDesc {
+  uint64_t lo, hi;      // as given
+  uint64_t nlo;         // first odd n >= max(lo, 3)  (>= hi: empty)
+  uint64_t jlo, jhi;    // valid bits [jlo, jhi)
+  int64_t w0;           // absolute word where tile 0's core starts (= jlo >> 5)
+  int64_t wend;         // one past the last absolute word holding a valid bit
+  uint32_t n_tiles;     // tiles of this range
+  uint32_t tile_base;   // global index of tile 0
+  uint32_t slot;        // result slot
+  uint32_t n_primes;    // primes p with p^2 < hi (p <= isqrt(hi - 1))
+  uint8_t *per_n_k;     // optional device output, index (n - nlo) / 2
+  uint64_t list_off, list_cap;  // this range's region of the list arena
+  uint64_t fail_off, fail_cap;  // this range's region of the failure arena
+  uint32_t sieve_only;  // 1: write the sieved words to bitmap_out, no scan
+  uint32_t pad;
+  uint32_t *bitmap_out; // sieve_only: word (a - w0) receives absolute word a
+};
+
+// Per-range aggregates, accumulated with atomics.
+struct ResultSlot {
+  unsigned long long hist[kMaxK];
+  unsigned long long first_n[kMaxK];
+  unsigned long long list_count;
+  unsigned long long fail_count;
+  unsigned long long pad[6];
+};
+
+// n whose n - 2^k left the tile's look-back window before a squarefree value
+// was found; the exact test continues at k0.
+struct Straggler {
+  uint64_t n;
+  uint32_t k0;
+  uint32_t req;
+};
+
+// Device header of a launch: sizes the persistent kernels read at run time,
+// so one captured graph serves every batch that fits the buffers.
+struct LaunchHeader {
+  uint32_t n_reqs;
+  uint32_t total_tiles;
+  uint32_t max_primes;      // max over requests of n_primes
+  uint32_t pad;
+  unsigned long long work_counter;  // tile queue head
+  unsigned long long strag_count;
+  uint32_t status;
+  uint32_t pad2;
+};
+
+struct Geometry {
+  uint32_t tw;        // core words per tile (2^(tile_log2 - 5))
+  uint32_t mw;        // look-back words (2^(margin_log2 - 6))
+  uint32_t kwin;      // largest k decided inside a window (= margin_log2)
+  uint32_t rec_t;     // record threshold T
+  uint32_t i_med;     // first prime index struck per tile (after the stamped ones)
+  uint32_t i_dense;   // primes [i_med, i_dense) are struck warp-cooperatively
+  uint32_t i_large;   // primes >= i_large come through buckets
+  uint32_t bucket_cap;
+  uint32_t tw_log2;   // log2(tw)
+  uint32_t bucket_auto;  // host only: the automatic capacity estimate
+};
+
+struct TileArgs {
+  PrimeTab pt;
+  Geometry g;
+  const ReqDesc *reqs;
+  LaunchHeader *hdr;
+  ResultSlot *slots;
+  uint64_t *list_n;
+  uint8_t *list_k;
+  uint64_t *fail_n;
+  Straggler *strag;
+  uint32_t strag_cap;
+  const uint32_t *bucket_count;
+  const uint32_t *bucket_data;
+};
+
+struct BucketArgs {
+  PrimeTab pt;
+  Geometry g;
+  const ReqDesc *reqs;
+  LaunchHeader *hdr;
+  uint32_t *bucket_count;
+  uint32_t *bucket_data;
+};
+
+struct StragArgs {
+  PrimeTab pt;
+  const ReqDesc *reqs;
+  LaunchHeader *hdr;
+  ResultSlot *slots;
+  uint64_t *list_n;
+  uint8_t *list_k;
+  uint64_t *fail_n;
+  const Straggler *strag;
+  uint32_t strag_cap;
+  uint32_t rec_t;
+};
+
+// Kernel launchers (defined in the .cu files).
+cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
+                        uint32_t *bucket_count, uint32_t n_tiles, cudaStream_t st);
+cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs,
+                               cudaStream_t st);
+cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem,
+                         bool per_n, cudaStream_t st);
+cudaError_t tile_kernel_setup(size_t smem);
+cudaError_t launch_stragglers(const StragArgs &a, uint32_t grid, cudaStream_t st);
+cudaError_t launch_points(PrimeTab pt, const uint64_t *pts, uint64_t count, uint8_t *out,
+                          uint32_t grid, cudaStream_t st);
+cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, uint64_t **d_inv,
+                              uint64_t **d_lim, uint32_t *n, uint32_t *n_div,
+                              cudaStream_t st);
+
+constexpr int kStampCount = 4;  // primes 3, 5, 7, 11 are stamped as word patterns
+
+}  // namespace sv
