@@ -134,6 +134,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(n_odd: int):
+    """DRAM bytes per launch of the tile kernel from the committed ncu capture,
+    scaled by odd n; None when the kernel source changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "tile_kernel_C2_traffic.json")
+    src = os.path.join(ROOT, "paper_2411_01964_gb300", "csrc", "tiles.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if sha != t.get("tiles_cu_sha256_16"):
+        return None
+    return t["dram_bytes_per_odd_n"] * n_odd
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -212,6 +229,7 @@ def main() -> int:
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--margin-log2", type=int, default=0)
     ap.add_argument("--large-prime-min", type=int, default=0)
+    ap.add_argument("--stamp-primes", type=int, default=0)
     ap.add_argument("--range", default="", help="LO:HI overrides the workload's range (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -247,7 +265,8 @@ def main() -> int:
     torch.cuda.set_stream(stream)
     knobs = {k: v for k, v in (("tile_log2", args.tile_log2), ("threads", args.threads),
                                  ("ctas_per_sm", args.ctas_per_sm), ("margin_log2", args.margin_log2),
-                                 ("large_prime_min", args.large_prime_min)) if v}
+                                 ("large_prime_min", args.large_prime_min),
+                                 ("stamp_primes", args.stamp_primes)) if v}
     v = Verifier(max_hi=hi + 1, stream=stream.cuda_stream, **knobs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -327,9 +346,9 @@ def main() -> int:
                    "l2": "flushed between steps (256 MiB write)",
                    "tile_log2": v.config.tile_log2, "threads": v.config.threads,
                    "margin_log2": v.config.margin_log2, "ctas_per_sm": v.config.ctas_per_sm,
-                   "large_prime_min": v.config.large_prime_min},
+                   "large_prime_min": v.config.large_prime_min, "stamp_primes": v.config.stamp_primes},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "int32 ops/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak, "traffic": measured_traffic(n_odd),
                      "kernel": "tile_kernel (sieve + scan, fused)",
                      "ops_per_odd_n": ops_per_n, "kernel_avg_ms": tile_avg_s * 1e3,
                      "kernel_share": tile_ms / total_ms if total_ms else None,

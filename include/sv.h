@@ -73,7 +73,8 @@ typedef struct sv_config {
     uint32_t bucket_capacity;    /* entries per tile bucket (grown automatically on overflow) */
     uint32_t record_k_threshold; /* T: every n with mink(n) >= T is listed (default 6) */
     uint32_t ctas_per_sm;        /* resident tile CTAs per SM (1 or 2) */
-    uint32_t reserved0;
+    uint32_t stamp_primes;       /* how many of the smallest odd primes (3, 5, 7, ...) are applied as
+                                    computed word patterns instead of atomic strikes: 2, 4, 6 or 8 */
     uint64_t list_capacity;      /* device list entries per range (grown on overflow) */
     uint64_t device_mem_budget;  /* bytes the serving loop may hold for requests in flight */
     void *cuda_stream;           /* cudaStream_t used for all work; NULL = a library stream */

@@ -28,7 +28,7 @@ FAIL_K = 255
 class sv_config(ctypes.Structure):
     _fields_ = [("tile_log2", u32), ("margin_log2", u32), ("threads", u32), ("large_prime_min", u32),
                 ("bucket_capacity", u32), ("record_k_threshold", u32), ("ctas_per_sm", u32),
-                ("reserved0", u32), ("list_capacity", u64), ("device_mem_budget", u64),
+                ("stamp_primes", u32), ("list_capacity", u64), ("device_mem_budget", u64),
                 ("cuda_stream", ctypes.c_void_p)]
 
 

@@ -80,11 +80,14 @@ uint32_t primes_upto(const sv_ctx *c, uint64_t x) {
 
 // Defaults and validation of the tuning knobs.
 sv_status normalise_config(sv_ctx *c, sv_config *k) {
-  if (k->tile_log2 == 0) k->tile_log2 = 20;
-  if (k->margin_log2 == 0) k->margin_log2 = 16;
-  if (k->threads == 0) k->threads = 1024;
+  // defaults: the fastest shape measured on GB300 for 2^33-odd-n ranges
+  if (k->tile_log2 == 0) k->tile_log2 = 19;
+  if (k->margin_log2 == 0) k->margin_log2 = 13;
+  if (k->threads == 0) k->threads = 512;
   if (k->record_k_threshold == 0) k->record_k_threshold = 6;
-  if (k->ctas_per_sm == 0) k->ctas_per_sm = 1;
+  if (k->ctas_per_sm == 0) k->ctas_per_sm = 2;
+  if (k->stamp_primes == 0) k->stamp_primes = 4;
+  if (k->stamp_primes > 8 || (k->stamp_primes & 1)) return SV_EINVAL;
   if (k->list_capacity == 0) k->list_capacity = 1ull << 16;
   if (k->device_mem_budget == 0) k->device_mem_budget = 8ull << 30;
   if (k->tile_log2 < 12 || k->tile_log2 > 20) return SV_EINVAL;
@@ -94,7 +97,7 @@ sv_status normalise_config(sv_ctx *c, sv_config *k) {
   if (k->ctas_per_sm > 4) return SV_EINVAL;
   const size_t tw = 1ull << (k->tile_log2 - 5), mw = 1ull << (k->margin_log2 - 6);
   const size_t smem = 4 * (tw + mw);
-  if (c->smem_optin && smem + 4096 > c->smem_optin) return SV_EINVAL;  // window + static data per CTA
+  if (c->smem_optin && smem + tile_static_smem() + 1024 > c->smem_optin) return SV_EINVAL;  // window + static
   if (k->large_prime_min == 0) k->large_prime_min = 1u << ((k->tile_log2 + 1) / 2);
   return SV_OK;
 }
@@ -118,16 +121,18 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   g.mw = 1u << (k.margin_log2 - 6);
   g.kwin = k.margin_log2;
   g.rec_t = k.record_k_threshold;
-  g.i_med = (uint32_t)kStampCount;
+  g.i_med = k.stamp_primes;  // the stamped primes are the table's first entries
   // dense: at least 32 strikes in a full window of 32*(tw+mw) bits
   const uint64_t dense_q = (uint64_t)g.tw + g.mw;
   uint32_t i = g.i_med;
-  while (i < c->n_primes && (uint64_t)c->h_p[i] * c->h_p[i] <= dense_q) ++i;
+  while (i < c->n_primes && i < g.i_med + (uint32_t)kMaxDensePrimes && (uint64_t)c->h_p[i] * c->h_p[i] <= dense_q)
+    ++i;
   g.i_dense = i;
   uint64_t lp = k.large_prime_min;
   if (span_bits) lp = std::max<uint64_t>(lp, host_isqrt(span_bits / 64) + 1);
   uint32_t il = primes_upto(c, lp - 1);
   if (il < g.i_dense) il = g.i_dense;
+  if (il > g.i_dense + (uint32_t)kMaxSparsePrimes) il = g.i_dense + (uint32_t)kMaxSparsePrimes;
   g.i_large = il;
   // expected bucket hits per full window: 32*(tw+mw) * sum_{large p} 1/p^2
   // (only sizes a buffer; overflow is detected and the launch repeated)
@@ -308,7 +313,8 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     if (grid > ws.total_tiles) grid = ws.total_tiles;
     {
       KTimer kt(c, kKTiles, st);
-      SV_TRY_CUDA(launch_tiles(t, c->cfg.threads, grid, smem, ws.any_per_n, st));
+      const int mode = ws.any_per_n ? 2 : (g.rec_t <= 5 ? 1 : 0);
+    SV_TRY_CUDA(launch_tiles(t, c->cfg.threads, grid, smem, mode, st));
       kt.done();
     }
     c->launches++;
@@ -871,21 +877,23 @@ sv_status sv_autotune(sv_ctx *c, uint64_t lo, uint64_t hi, sv_config *chosen) {
   sv_range_result res;
   std::memset(&res, 0, sizeof(res));
   sv_range_result *outs[1] = {&res};
-  const uint32_t tiles[] = {17, 18, 19, 20};
+  const uint32_t tiles[] = {18, 19, 20};
   const uint32_t threads[] = {512, 1024};
   const uint32_t ctas[] = {1, 2};
-  const uint32_t margins[] = {14, 16};
+  const uint32_t margins[] = {13, 16};
+  const uint32_t stamps[] = {2, 4, 6, 8};
   for (uint32_t tl : tiles)
     for (uint32_t th : threads)
       for (uint32_t cp : ctas)
         for (uint32_t ml : margins)
-          for (uint32_t lp_shift = 0; lp_shift < 2; ++lp_shift) {
+          for (uint32_t ns : stamps) {
             sv_config k = base;
             k.tile_log2 = tl;
             k.threads = th;
             k.ctas_per_sm = cp;
+            k.stamp_primes = ns;
             k.margin_log2 = ml < tl + 1 ? ml : tl + 1;
-            k.large_prime_min = 1u << ((tl + 1) / 2 + lp_shift);
+            k.large_prime_min = 1u << ((tl + 1) / 2);
             k.bucket_capacity = 0;
             const size_t smem = 4ull * ((1ull << (tl - 5)) + (1ull << (k.margin_log2 - 6)));
             if (cp * (smem + 4096) > c->smem_optin + 4096 || (size_t)cp * th > 2048) continue;

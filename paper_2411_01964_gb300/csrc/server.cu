@@ -99,6 +99,10 @@ class Server {
     for (auto &s : slots_) {
       if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess) return SV_ECUDA;
       if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) return SV_ECUDA;
+      // staging for the points of one launch, sized once: fill() packs several
+      // requests into it and must never see it reallocated
+      if (s.ws.h_points.ensure(kMaxPointsPerLaunch) || s.ws.h_points_out.ensure(kMaxPointsPerLaunch))
+        return SV_ENOMEM;
     }
     th_ = std::thread([this] { loop(); });
     return SV_OK;
@@ -286,7 +290,6 @@ class Server {
         const uint64_t room = kMaxPointsPerLaunch - s.npoints;
         if (room == 0) break;
         const uint64_t cnt = std::min<uint64_t>(room, r.r.n_points - r.next_point);
-        if (s.ws.h_points.ensure(s.npoints + cnt) || s.ws.h_points_out.ensure(s.npoints + cnt)) break;
         std::memcpy(s.ws.h_points.p + s.npoints, r.r.points + r.next_point, 8 * cnt);
         s.pitems.push_back({r.ticket, r.next_point, cnt, s.npoints});
         s.npoints += cnt;

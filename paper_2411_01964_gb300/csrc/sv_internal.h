@@ -143,9 +143,12 @@ cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t n_tiles, cudaStream_t st);
 cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs,
                                cudaStream_t st);
-cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem,
-                         bool per_n, cudaStream_t st);
+// mode 0: lean scan (lists from k >= 6, no per-n output); 1: general scan;
+// 2: general scan writing the per-n output.
+cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem, int mode,
+                         cudaStream_t st);
 cudaError_t tile_kernel_setup(size_t smem);
+size_t tile_static_smem();
 cudaError_t launch_stragglers(const StragArgs &a, uint32_t grid, cudaStream_t st);
 cudaError_t launch_points(PrimeTab pt, const uint64_t *pts, uint64_t count, uint8_t *out,
                           uint32_t grid, cudaStream_t st);
@@ -153,6 +156,7 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
                               uint64_t **d_lim, uint32_t *n, uint32_t *n_div,
                               cudaStream_t st);
 
-constexpr int kStampCount = 4;  // primes 3, 5, 7, 11 are stamped as word patterns
+constexpr int kMaxDensePrimes = 32;  // must match the tile kernel's shared arrays (one warp)
+constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)
 
 }  // namespace sv

@@ -6,17 +6,22 @@
 // mw words below it (the paper keeps the preceding interval for the same
 // purpose, Sec. 3 after Algorithm 2).  Per tile:
 //   1. stamp:  every window word starts as the AND of the periodic strike
-//              patterns of p = 3, 5, 7, 11 (computed, not loaded);
-//   2. strike: primes 13 <= p < large_prime_min clear their odd multiples of
-//              p^2 with shared-memory atomicAnd (warp-cooperative while a
-//              prime has >= 32 hits per tile, one thread per prime above);
-//              larger primes arrive as precomputed bit offsets in the tile's
-//              bucket (bucket_fill_kernel);
+//              patterns of the NS smallest odd primes (computed by the word's
+//              owner, not loaded; NS = sv_config.stamp_primes);
+//   2. strike: the next primes up to large_prime_min clear their odd multiples of
+//              p^2 with shared-memory atomicAnd: "dense" primes (>= 32 hits
+//              per window) have their strikes spread over all threads of the
+//              CTA, sparser ones take one thread per prime; larger primes
+//              arrive as precomputed bit offsets in the tile's bucket
+//              (bucket_fill_kernel);
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
 //              flags of n - 2^k are word i shifted by 2^(k-1) bits: a funnel
 //              shift of (w[i-1], w[i]) for k <= 5, the word w[i - 2^(k-6)] for
-//              6 <= k <= kwin.  unresolved &= ~flags; hist[k] += popc(newly).
-//              n still unresolved after kwin go to the exact straggler test;
+//              6 <= k <= kwin.  unresolved &= ~flags; hist[k] += popc(newly);
+//              the warp stops at the first k where no lane has an unresolved
+//              n.  n still unresolved after kwin go to the exact straggler
+//              test.  Each warp records its first occurrence of each frequent
+//              exponent by ballot until it has seen them all;
 //   4. reduce: per-tile histogram and first occurrences into the range's
 //              result slot (Sec. 3 "Collecting the results").
 // The bitmap never leaves shared memory.
@@ -44,7 +49,17 @@ __device__ __forceinline__ uint64_t first_strike(uint64_t A, uint64_t q, uint64_
   return (c >= r) ? (c - r) : (c + q - r);
 }
 
-// The stamped primes: q = p^2 and the 32-bit pattern with a 1 every q bits.
+// The stamped primes (the smallest ones, applied by the word's owner as a
+// computed pattern instead of shared-memory atomics): q = p^2 and the 32-bit
+// pattern with a 1 every q bits (a single bit once q >= 32).
+__host__ __device__ constexpr uint32_t stamp_p(int s) {
+  return s == 0 ? 3 : s == 1 ? 5 : s == 2 ? 7 : s == 3 ? 11 : s == 4 ? 13 : s == 5 ? 17 : s == 6 ? 19 : 23;
+}
+__host__ __device__ constexpr uint32_t stamp_rep(uint32_t q) {
+  uint32_t r = 0;
+  for (uint32_t b = 0; b < 32; b += q) r |= 1u << b;
+  return r;
+}
 __device__ __forceinline__ uint32_t stamp_first(uint64_t abit, uint32_t q) {
   const uint32_t r = (uint32_t)(abit % q);
   const uint32_t c = (q - 1) >> 1;
@@ -53,9 +68,34 @@ __device__ __forceinline__ uint32_t stamp_first(uint64_t abit, uint32_t q) {
 __device__ __forceinline__ uint32_t stamp_step(uint32_t j, uint32_t d, uint32_t q) {
   return (j >= d) ? (j - d) : (j + q - d);
 }
-constexpr uint32_t kQ0 = 9, kQ1 = 25, kQ2 = 49, kQ3 = 121;
-constexpr uint32_t kRep0 = (1u << 0) | (1u << 9) | (1u << 18) | (1u << 27);
-constexpr uint32_t kRep1 = (1u << 0) | (1u << 25);
+
+// Window words [nz, nwords) <- AND of the NS stamped patterns; thread tid
+// takes words tid, tid + S, ...  j[s] is the offset of prime s's first struck
+// bit in the current word (>= 32: none); moving S words subtracts 32*S mod q.
+template <int NS>
+__device__ __forceinline__ void stamp_window(uint32_t *win, uint32_t nz, uint32_t nwords, int64_t wstart) {
+  const uint32_t S = blockDim.x;
+  uint32_t i = nz + threadIdx.x;
+  if (i >= nwords) return;
+  const uint64_t abit = 32ull * (uint64_t)(wstart + (int64_t)i);
+  uint32_t j[NS], d[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const uint32_t q = stamp_p(s) * stamp_p(s);
+    j[s] = stamp_first(abit, q);
+    d[s] = (32u * S) % q;
+  }
+  for (; i < nwords; i += S) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const uint32_t q = stamp_p(s) * stamp_p(s);
+      m |= __funnelshift_lc(0u, stamp_rep(q), j[s]);
+      j[s] = stamp_step(j[s], d[s], q);
+    }
+    win[i] = ~m;
+  }
+}
 
 // Bits b of the word starting at bit J0 with jlo <= J0 + b < jhi.
 __device__ __forceinline__ uint32_t valid_mask(uint64_t J0, uint64_t jlo, uint64_t jhi) {
@@ -69,8 +109,9 @@ __device__ __forceinline__ uint32_t valid_mask(uint64_t J0, uint64_t jlo, uint64
   return m;
 }
 
+// Clear bit b of the window: the mask is 0xFFFFFFFE rotated left by b mod 32.
 __device__ __forceinline__ void strike(uint32_t *win, uint32_t b) {
-  atomicAnd(&win[b >> 5], ~(1u << (b & 31u)));
+  atomicAnd(&win[b >> 5], __funnelshift_l(0xFFFFFFFEu, 0xFFFFFFFEu, b));
 }
 
 // ---------------------------------------------------------------------------
@@ -196,15 +237,33 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
 // The tile kernel.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kMaxDense = 32;  // dense primes (>= 32 strikes per window) per tile: one warp
+
+constexpr uint32_t kDeferCap = 128;  // words left unresolved after k = 5, per tile
+constexpr uint32_t kMaxSparse = kMaxSparsePrimes;  // primes struck one thread each, per tile
+
 struct ScanShared {
   unsigned long long hist[kMaxK];
   unsigned long long first[kMaxK];
   ReqDesc req;
   uint32_t tile;
+  uint32_t next_tile;              // prefetched during the previous tile's scan
   uint32_t req_idx;
+  uint32_t n_strag;                // stragglers this tile sent to the exact test
+  uint32_t need;                   // k <= 5 whose first occurrence this tile may still improve
+  uint32_t defer_n;
+  // the dense primes' strikes of this tile, numbered consecutively prime by
+  // prime: prime d owns numbers [dense_pre[d], dense_pre[d+1]), its strike
+  // number x is bit dense_off[d] + (x - dense_pre[d]) * dense_q[d]
+  uint32_t dense_q[kMaxDense];
+  uint32_t dense_off[kMaxDense];
+  uint32_t dense_pre[kMaxDense + 1];
+  uint32_t defer_i[kDeferCap];     // window index of a deferred word
+  uint32_t defer_u[kDeferCap];     // its n still unresolved after k = 5
+  uint32_t sparse_off[kMaxSparse]; // first struck bit of each sparse prime (>= nbits: none)
+  uint32_t sparse_q[kMaxSparse];
 };
 
 // Record the n of hit (mink = k, k >= T) in the range's list and first_n.
@@ -224,8 +283,9 @@ __device__ __noinline__ void list_append(const TileArgs &a, const ReqDesc &R, ui
   }
 }
 
-__device__ __noinline__ void straggler_push(const TileArgs &a, uint32_t unres, uint64_t J0,
-                                            uint32_t k0, uint32_t req) {
+__device__ __noinline__ void straggler_push(const TileArgs &a, ScanShared &sh, uint32_t unres, uint64_t J0,
+                                            uint32_t k0) {
+  atomicAdd(&sh.n_strag, (uint32_t)__popc(unres));
   while (unres) {
     const uint32_t b = __ffs(unres) - 1;
     unres &= unres - 1;
@@ -234,7 +294,7 @@ __device__ __noinline__ void straggler_push(const TileArgs &a, uint32_t unres, u
       Straggler s;
       s.n = 2ull * (J0 + b) + 1ull;
       s.k0 = k0;
-      s.req = req;
+      s.req = sh.req_idx;
       a.strag[idx] = s;
     } else {
       atomicOr(&a.hdr->status, kStStragOverflow);
@@ -255,50 +315,270 @@ __device__ __forceinline__ void write_per_n(uint8_t *out, uint64_t J0, uint64_t 
   }
 }
 
-template <int K, bool PER_N>
-__device__ __forceinline__ void scan_step(uint32_t sf, uint32_t &unres, uint32_t &cnt, uint32_t &need,
-                                          uint32_t pl[6], uint64_t J0, uint32_t rec_t,
-                                          ScanShared &sh, const TileArgs &a) {
+// One step of the word-parallel Algorithm 2 for k <= 5 (sf = flags of n - 2^k).
+//   LEAN: k = 1 is not counted (derived at the end of the tile from the
+//         number of valid n) and lists start at k >= 6 (T >= 6).
+template <int K, bool LEAN, bool PER_N>
+__device__ __forceinline__ void scan_step(uint32_t sf, uint32_t &unres, uint32_t &cnt, uint32_t pl[6],
+                                          const TileArgs &a, ScanShared &sh, int64_t aw, uint32_t rec_t) {
   const uint32_t hit = unres & sf;
   unres &= ~sf;
-  cnt += __popc(hit);
+  if (!(LEAN && K == 1)) cnt += __popc(hit);
   if (PER_N) {
 #pragma unroll
     for (int j = 0; j < 6; ++j)
       if ((K >> j) & 1) pl[j] |= hit;
   }
-  if (hit) {
-    if (need & (1u << K)) {
-      need &= ~(1u << K);
-      atomicMin(&sh.first[K], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(hit) - 1)) + 1ull));
+  if (!LEAN && (uint32_t)K >= rec_t && hit) list_append(a, sh.req, hit, 32ull * (uint64_t)aw, (uint32_t)K);
+}
+
+// k = 6 .. kwin (rare): whole-word look-back reads; counts, first occurrences
+// below T and lists go straight to shared/global atomics.
+template <bool PER_N>
+__device__ __noinline__ uint32_t scan_tail(const uint32_t *win, uint32_t i, bool act, uint32_t unres,
+                                           uint32_t pl[6], const TileArgs &a, ScanShared &sh, int64_t aw,
+                                           uint32_t kwin, uint32_t rec_t) {
+  const uint64_t J0 = 32ull * (uint64_t)aw;
+  for (uint32_t k = 6; k <= kwin && __any_sync(0xFFFFFFFFu, unres); ++k) {
+    const uint32_t sf = act ? win[i - (1u << (k - 6))] : 0u;
+    const uint32_t hit = unres & sf;
+    unres &= ~sf;
+    if (PER_N) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        if ((k >> j) & 1u) pl[j] |= hit;
     }
-    if ((uint32_t)K >= rec_t) list_append(a, sh.req, hit, J0, (uint32_t)K);
+    if (hit) {
+      atomicAdd(&sh.hist[k], (unsigned long long)__popc(hit));
+      if (k < rec_t)
+        atomicMin(&sh.first[k], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(hit) - 1)) + 1ull));
+      else
+        list_append(a, sh.req, hit, J0, k);
+    }
+  }
+  if (unres) straggler_push(a, sh, unres, J0, kwin + 1u);
+  return unres;
+}
+
+// Record, for each k with a bit in `need`, the warp's first n with mink = k.
+// need is warp-uniform; a warp visits its words in increasing order, so its
+// first hit for k is its smallest, and the minimum over warps is the tile's.
+template <int K>
+__device__ __forceinline__ void record_first(uint32_t hit, uint32_t &need, ScanShared &sh, int64_t aw) {
+  if (need & (1u << K)) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hit != 0);
+    if (bal) {
+      if ((threadIdx.x & 31u) == (uint32_t)(__ffs(bal) - 1))
+        atomicMin(&sh.first[K], (unsigned long long)(64ull * (uint64_t)aw + 2ull * (uint64_t)(__ffs(hit) - 1) + 1ull));
+      need &= ~(1u << K);
+    }
   }
 }
 
-template <bool PER_N>
+// One warp-iteration of the scan: lane's word i.  REC: some of the frequent
+// exponents (k <= 5) still lack this warp's first occurrence.
+template <bool LEAN, bool PER_N, bool REC>
+__device__ __forceinline__ void scan_word(const uint32_t *win, uint32_t i, bool act, int64_t aw, uint32_t valid,
+                                          uint32_t &need, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t &c4,
+                                          uint32_t &c5, const TileArgs &a, ScanShared &sh) {
+  const uint32_t kwin = a.g.kwin, rec_t = a.g.rec_t;
+  const uint32_t w = act ? win[i] : 0u;
+  const uint32_t wp = act ? win[i - 1] : 0u;
+  uint32_t unres = valid;
+  uint32_t pl[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+  uint32_t h;
+#define SV_STEP(K, SF, CNT)                                     \
+  h = unres & (SF);                                             \
+  unres &= ~(SF);                                               \
+  if (!(LEAN && K == 1)) CNT += __popc(h);                      \
+  if (PER_N) {                                                  \
+    _Pragma("unroll") for (int j = 0; j < 6; ++j) if ((K >> j) & 1) pl[j] |= h; \
+  }                                                             \
+  if (REC) record_first<K>(h, need, sh, aw);                    \
+  if (!LEAN && (uint32_t)K >= rec_t && h) list_append(a, sh.req, h, 32ull * (uint64_t)aw, (uint32_t)K);
+  SV_STEP(1, __funnelshift_l(wp, w, 1), c1)
+  if (__any_sync(0xFFFFFFFFu, unres)) {
+    SV_STEP(2, __funnelshift_l(wp, w, 2), c2)
+    if (__any_sync(0xFFFFFFFFu, unres)) {
+      SV_STEP(3, __funnelshift_l(wp, w, 4), c3)
+      if (__any_sync(0xFFFFFFFFu, unres)) {
+        SV_STEP(4, __funnelshift_l(wp, w, 8), c4)
+        if (__any_sync(0xFFFFFFFFu, unres)) {
+          SV_STEP(5, __funnelshift_l(wp, w, 16), c5)
+          if (__any_sync(0xFFFFFFFFu, unres)) scan_tail<PER_N>(win, i, act, unres, pl, a, sh, aw, kwin, rec_t);
+        }
+      }
+    }
+  }
+#undef SV_STEP
+  if (PER_N && sh.req.per_n_k) write_per_n(sh.req.per_n_k, 32ull * (uint64_t)aw, sh.req.jlo, valid, pl);
+}
+
+// One thread finishes one word whose n (bits u) are unresolved after k = 5:
+// k = 6 .. kwin by whole-word look-back, then the exact test for the rest.
+__device__ __noinline__ void finish_word(const uint32_t *win, uint32_t i, uint32_t u, int64_t aw, const TileArgs &a,
+                                         ScanShared &sh) {
+  const uint64_t J0 = 32ull * (uint64_t)aw;
+  const uint32_t kwin = a.g.kwin, rec_t = a.g.rec_t;
+  for (uint32_t k = 6; k <= kwin && u; ++k) {
+    const uint32_t h = u & win[i - (1u << (k - 6))];
+    u ^= h;
+    if (h) {
+      atomicAdd(&sh.hist[k], (unsigned long long)__popc(h));
+      if (k < rec_t)
+        atomicMin(&sh.first[k], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(h) - 1)) + 1ull));
+      else
+        list_append(a, sh.req, h, J0, k);
+    }
+  }
+  if (u) straggler_push(a, sh, u, J0, kwin + 1u);
+}
+
+__device__ __forceinline__ void defer_word(const uint32_t *win, uint32_t i, uint32_t u, int64_t aw, const TileArgs &a,
+                                           ScanShared &sh) {
+  const uint32_t e = atomicAdd(&sh.defer_n, 1u);
+  if (e < kDeferCap) {
+    sh.defer_i[e] = i;
+    sh.defer_u[e] = u;
+  } else {
+    finish_word(win, i, u, aw, a, sh);
+  }
+}
+
+// k = K for two words at once (independent chains for the scheduler).
+template <int K>
+__device__ __forceinline__ uint32_t step2(uint32_t p0, uint32_t w0, uint32_t p1, uint32_t w1, uint32_t &u0,
+                                          uint32_t &u1) {
+  const uint32_t h0 = u0 & __funnelshift_l(p0, w0, 1u << (K - 1));
+  const uint32_t h1 = u1 & __funnelshift_l(p1, w1, 1u << (K - 1));
+  u0 ^= h0;
+  u1 ^= h1;
+  return (uint32_t)(__popc(h0) + __popc(h1));
+}
+
+// The lean scan (no per-n output, lists from k >= 6): each lane takes two
+// words per iteration, k = 1 is not counted, and words still unresolved
+// after k = 5 are queued for finish_word after the loop.  Tiles that may
+// still hold a range's first occurrence of some k <= 5 use scan_word.
+__device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileArgs &a, ScanShared &sh,
+                                               int64_t wstart, uint32_t nwords, uint32_t ifl, uint32_t nfull) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t mw = a.g.mw;
+  uint32_t need = sh.need;
+  uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  for (uint32_t ib = mw + warp * 64u; ib < nwords; ib += nwarps * 64u) {
+    const uint32_t i0 = ib + lane, i1 = i0 + 32u;
+    const bool a0 = i0 < nwords, a1 = i1 < nwords;
+    const int64_t aw0 = wstart + (int64_t)i0, aw1 = aw0 + 32;
+    uint32_t v0, v1;
+    if (i0 - ifl < nfull) v0 = 0xFFFFFFFFu;
+    else v0 = a0 ? valid_mask(32ull * (uint64_t)aw0, sh.req.jlo, sh.req.jhi) : 0u;
+    if (i1 - ifl < nfull) v1 = 0xFFFFFFFFu;
+    else v1 = a1 ? valid_mask(32ull * (uint64_t)aw1, sh.req.jlo, sh.req.jhi) : 0u;
+    if (need) {
+      scan_word<true, false, true>(win, i0, a0, aw0, v0, need, c1, c2, c3, c4, c5, a, sh);
+      scan_word<true, false, true>(win, i1, a1, aw1, v1, need, c1, c2, c3, c4, c5, a, sh);
+      continue;
+    }
+    const uint32_t w0 = a0 ? win[i0] : 0u, p0 = a0 ? win[i0 - 1] : 0u;
+    const uint32_t w1 = a1 ? win[i1] : 0u, p1 = a1 ? win[i1 - 1] : 0u;
+    // k = 1..4 without votes: nearly every 64-word warp step needs k = 4
+    uint32_t u0 = v0 & ~__funnelshift_l(p0, w0, 1);
+    uint32_t u1 = v1 & ~__funnelshift_l(p1, w1, 1);
+    c2 += step2<2>(p0, w0, p1, w1, u0, u1);
+    c3 += step2<3>(p0, w0, p1, w1, u0, u1);
+    c4 += step2<4>(p0, w0, p1, w1, u0, u1);
+    if (__any_sync(0xFFFFFFFFu, u0 | u1)) {
+      c5 += step2<5>(p0, w0, p1, w1, u0, u1);
+      if (u0) defer_word(win, i0, u0, aw0, a, sh);
+      if (u1) defer_word(win, i1, u1, aw1, a, sh);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
+    c3 += __shfl_xor_sync(0xFFFFFFFFu, c3, o);
+    c4 += __shfl_xor_sync(0xFFFFFFFFu, c4, o);
+    c5 += __shfl_xor_sync(0xFFFFFFFFu, c5, o);
+  }
+  if (lane == 0) {
+    if (c2) atomicAdd(&sh.hist[2], (unsigned long long)c2);
+    if (c3) atomicAdd(&sh.hist[3], (unsigned long long)c3);
+    if (c4) atomicAdd(&sh.hist[4], (unsigned long long)c4);
+    if (c5) atomicAdd(&sh.hist[5], (unsigned long long)c5);
+  }
+}
+
+template <bool LEAN, bool PER_N>
+__device__ __forceinline__ void scan_tile(const uint32_t *win, const TileArgs &a, ScanShared &sh, int64_t wstart,
+                                          uint32_t nwords, uint32_t ifl, uint32_t nfull) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const Geometry &g = a.g;
+  // frequent exponents whose first occurrence is taken here: k = 1 .. min(T-1, kwin, 5)
+  uint32_t need = sh.need;
+  uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  for (uint32_t ib = g.mw + warp * 32u; ib < nwords; ib += nwarps * 32u) {
+    const uint32_t i = ib + lane;
+    const bool act = i < nwords;
+    const int64_t aw = wstart + (int64_t)i;
+    uint32_t valid;
+    if (i - ifl < nfull) valid = 0xFFFFFFFFu;
+    else valid = act ? valid_mask(32ull * (uint64_t)aw, sh.req.jlo, sh.req.jhi) : 0u;
+    if (need)
+      scan_word<LEAN, PER_N, true>(win, i, act, aw, valid, need, c1, c2, c3, c4, c5, a, sh);
+    else
+      scan_word<LEAN, PER_N, false>(win, i, act, aw, valid, need, c1, c2, c3, c4, c5, a, sh);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if (!LEAN) c1 += __shfl_xor_sync(0xFFFFFFFFu, c1, o);
+    c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
+    c3 += __shfl_xor_sync(0xFFFFFFFFu, c3, o);
+    c4 += __shfl_xor_sync(0xFFFFFFFFu, c4, o);
+    c5 += __shfl_xor_sync(0xFFFFFFFFu, c5, o);
+  }
+  if (lane == 0) {
+    if (!LEAN && c1) atomicAdd(&sh.hist[1], (unsigned long long)c1);
+    if (c2) atomicAdd(&sh.hist[2], (unsigned long long)c2);
+    if (c3) atomicAdd(&sh.hist[3], (unsigned long long)c3);
+    if (c4) atomicAdd(&sh.hist[4], (unsigned long long)c4);
+    if (c5) atomicAdd(&sh.hist[5], (unsigned long long)c5);
+  }
+}
+
+// MODE 0: lean scan (no per-n output, lists from k >= 6); 1: general scan;
+// 2: general scan with the per-n output.  NS: number of stamped primes.
+template <int MODE, int NS>
 __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
   extern __shared__ uint32_t win[];
   __shared__ ScanShared sh;
+  constexpr bool LEAN = (MODE == 0);
+  constexpr bool PER_N = (MODE == 2);
 
   const uint32_t tid = threadIdx.x, S = blockDim.x;
-  const uint32_t lane = tid & 31u, warp = tid >> 5, nwarps = S >> 5;
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
   const Geometry g = a.g;
   const uint32_t total = a.hdr->total_tiles;
   const uint32_t n_reqs = a.hdr->n_reqs;
-
-  // per-block stamping strides: moving S words moves 32*S bits
-  const uint32_t d0 = (32u * S) % kQ0, d1 = (32u * S) % kQ1;
-  const uint32_t d2 = (32u * S) % kQ2, d3 = (32u * S) % kQ3;
+  const uint32_t nd = g.i_dense - g.i_med;  // <= kMaxDense (host guarantees)
+  // frequent exponents whose first occurrence is searched per tile: k = 1 .. kfirst
+  const uint32_t kfirst = min(min(g.rec_t, g.kwin + 1u) - 1u, 5u);
 
   if (tid < kMaxK) {
     sh.hist[tid] = 0ull;
     sh.first[tid] = kNoN;
   }
+  if (tid == 0) {
+    sh.n_strag = 0;
+    sh.defer_n = 0;
+    sh.req_idx = 0xFFFFFFFFu;
+    sh.next_tile = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+  }
+  __syncthreads();
 
   for (;;) {
     if (tid == 0) {
-      const uint32_t t = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+      const uint32_t t = sh.next_tile;
       sh.tile = t;
       if (t < total) {
         uint32_t lo = 0, hi = n_reqs;
@@ -306,8 +586,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
           const uint32_t mid = (lo + hi) >> 1;
           if (a.reqs[mid].tile_base <= t) lo = mid; else hi = mid;
         }
-        sh.req_idx = lo;
-        sh.req = a.reqs[lo];
+        if (lo != sh.req_idx) {
+          sh.req_idx = lo;
+          sh.req = a.reqs[lo];
+        }
       }
     }
     __syncthreads();
@@ -316,7 +598,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     const ReqDesc &R = sh.req;
     const uint32_t t = gt - R.tile_base;
     if (t >= R.n_tiles) {  // bounds check: never expected
-      if (tid == 0) atomicOr(&a.hdr->status, kStBadTile);
+      if (tid == 0) {
+        atomicOr(&a.hdr->status, kStBadTile);
+        sh.next_tile = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+      }
       __syncthreads();
       continue;
     }
@@ -324,164 +609,214 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     const int64_t twe = min(tws + (int64_t)g.tw, R.wend);
     const int64_t wstart = tws - (int64_t)g.mw;
     const uint32_t nwords = (uint32_t)(twe - wstart);
+    const int64_t aw0 = wstart < 0 ? 0 : wstart;
+    const uint64_t A = 32ull * (uint64_t)aw0;
+    const uint32_t abias = 32u * (uint32_t)(aw0 - wstart);
+    const uint32_t nbits = 32u * nwords;
+    // n of the tile's first valid bit: a first occurrence already recorded
+    // below it (by any tile) cannot be improved here
+    const unsigned long long n_first =
+        2ull * max((unsigned long long)R.jlo, 32ull * (unsigned long long)tws) + 1ull;
+    unsigned long long known[5] = {0, 0, 0, 0, 0};
+    if (tid == 0 && !R.sieve_only)
+      for (uint32_t k = 1; k <= kfirst; ++k) known[k - 1] = __ldcg(&a.slots[R.slot].first_n[k]);
 
-    // ---- 1. stamp p = 3, 5, 7, 11 --------------------------------------
+    // ---- 1. stamp the smallest primes; the dense primes' first strikes -------
+    if (warp == 0) {
+      uint32_t q = 1, off = 0, cnt = 0;
+      if (lane < nd) {
+        const uint64_t p = a.pt.p[g.i_med + lane];
+        q = (uint32_t)(p * p);
+        off = abias + (uint32_t)first_strike(A, (uint64_t)q, a.pt.mu[g.i_med + lane]);
+        cnt = off < nbits ? (nbits - off + q - 1) / q : 0u;
+      }
+      uint32_t incl = cnt;  // inclusive prefix over the dense primes
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      if (lane < nd) {
+        sh.dense_q[lane] = q;
+        sh.dense_off[lane] = off;
+        sh.dense_pre[lane] = incl - cnt;
+      }
+      if (lane == 31) sh.dense_pre[nd] = incl;  // lanes >= nd add nothing: the total
+    }
     const uint32_t nz = (wstart < 0) ? (uint32_t)min((int64_t)nwords, -wstart) : 0u;
     for (uint32_t i = tid; i < nz; i += S) win[i] = 0u;  // integers below 1
-    {
-      uint32_t i = nz + tid;
-      if (i < nwords) {
-        const uint64_t abit = 32ull * (uint64_t)(wstart + (int64_t)i);
-        uint32_t j0 = stamp_first(abit, kQ0), j1 = stamp_first(abit, kQ1);
-        uint32_t j2 = stamp_first(abit, kQ2), j3 = stamp_first(abit, kQ3);
-        for (; i < nwords; i += S) {
-          const uint32_t m = __funnelshift_lc(0u, kRep0, j0) | __funnelshift_lc(0u, kRep1, j1) |
-                             __funnelshift_lc(0u, 1u, j2) | __funnelshift_lc(0u, 1u, j3);
-          win[i] = ~m;
-          j0 = stamp_step(j0, d0, kQ0);
-          j1 = stamp_step(j1, d1, kQ1);
-          j2 = stamp_step(j2, d2, kQ2);
-          j3 = stamp_step(j3, d3, kQ3);
-        }
-      }
+    // sparse primes: their first strikes, and the tile's bucket entries, are
+    // fetched here so that the global-memory latency overlaps the stamping
+    const uint32_t i_large = min(g.i_large, max(R.n_primes, g.i_dense));
+    const uint32_t n_sparse = i_large - g.i_dense;  // <= kMaxSparse (host guarantees)
+    for (uint32_t j = tid; j < n_sparse; j += S) {
+      const uint64_t p = a.pt.p[g.i_dense + j];
+      const uint64_t q = p * p;
+      sh.sparse_off[j] = abias + (uint32_t)first_strike(A, q, a.pt.mu[g.i_dense + j]);
+      sh.sparse_q[j] = (uint32_t)q;
+    }
+    const uint32_t *bd = a.bucket_data + (size_t)gt * g.bucket_cap;
+    const uint32_t nb = min(a.bucket_count[gt], g.bucket_cap);
+    const uint32_t bv0 = tid < g.bucket_cap ? bd[tid] : 0u;
+    const uint32_t bv1 = tid + S < g.bucket_cap ? bd[tid + S] : 0u;
+    stamp_window<NS>(win, nz, nwords, wstart);
+    if (tid == 0) {
+      uint32_t need = 0;
+      for (uint32_t k = 1; k <= kfirst; ++k)
+        if (known[k - 1] > n_first) need |= 1u << k;
+      sh.need = need;
     }
     __syncthreads();
 
-    // ---- 2. strike the medium primes, apply the bucket ------------------
+    // ---- 2. strikes: dense primes spread over all threads, sparse primes one
+    //         thread each, large primes from the tile's bucket ---------------
     {
-      const int64_t aw = wstart < 0 ? 0 : wstart;
-      const uint64_t A = 32ull * (uint64_t)aw;
-      const uint32_t abias = 32u * (uint32_t)(aw - wstart);
-      const uint32_t nbits = 32u * nwords;
-      const uint32_t np = R.n_primes;
-      const uint32_t i_dense = min(g.i_dense, np), i_large = min(g.i_large, np);
-      for (uint32_t pi = g.i_med + warp; pi < i_dense; pi += nwarps) {
-        const uint64_t p = a.pt.p[pi];
-        const uint64_t q = p * p;
-        const uint32_t q32 = (uint32_t)q;
-        const uint32_t off = abias + (uint32_t)first_strike(A, q, a.pt.mu[pi]);
-        for (uint32_t b = off + lane * q32; b < nbits; b += 32u * q32) strike(win, b);
+      // dense primes: warp w takes strike numbers [X w / nwarps, X (w+1) / nwarps),
+      // its lanes every 32nd; the prime d of a number only moves forward
+      const uint32_t nwarps = S >> 5;
+      const uint32_t X = sh.dense_pre[nd];
+      const uint32_t x1 = (X * (warp + 1)) / nwarps;
+      uint32_t x = (X * warp) / nwarps + lane;
+      if (x < x1) {
+        uint32_t d = 0;
+        while (sh.dense_pre[d + 1] <= x) ++d;
+        uint32_t pn = sh.dense_pre[d + 1], p0 = sh.dense_pre[d], q = sh.dense_q[d], off = sh.dense_off[d];
+        for (; x < x1; x += 32u) {
+          if (x >= pn) {
+            do {
+              ++d;
+              pn = sh.dense_pre[d + 1];
+            } while (x >= pn);
+            p0 = sh.dense_pre[d];
+            q = sh.dense_q[d];
+            off = sh.dense_off[d];
+          }
+          strike(win, off + (x - p0) * q);
+        }
       }
-      for (uint32_t pi = max(i_dense, g.i_med) + tid; pi < i_large; pi += S) {
-        const uint64_t p = a.pt.p[pi];
-        const uint64_t q = p * p;
-        for (uint64_t b = abias + first_strike(A, q, a.pt.mu[pi]); b < nbits; b += q)
-          strike(win, (uint32_t)b);
+      for (uint32_t j = tid; j < n_sparse; j += S) {
+        const uint32_t q = sh.sparse_q[j];
+        for (uint32_t b = sh.sparse_off[j]; b < nbits; b += q) strike(win, b);
       }
-      const uint32_t nb = min(a.bucket_count[gt], g.bucket_cap);
-      const uint32_t *bd = a.bucket_data + (size_t)gt * g.bucket_cap;
       for (uint32_t e = tid; e < nb; e += S) {
-        const uint32_t b = bd[e];
+        const uint32_t b = e < S ? bv0 : (e < 2 * S ? bv1 : bd[e]);
         if (b < nbits) strike(win, b);
         else atomicOr(&a.hdr->status, kStBadTile);
       }
     }
     __syncthreads();
 
+    // the next tile's index, fetched while this tile is scanned
+    uint32_t next = 0;
+    if (tid == 0) next = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+
     if (R.sieve_only) {
-      // ---- Algorithm 1 alone: write the core words --------------------
+      // ---- Algorithm 1 alone: write the core words ------------------------
       for (uint32_t i = g.mw + tid; i < nwords; i += S) {
         const int64_t aw = wstart + (int64_t)i;
         const uint32_t v = valid_mask(32ull * (uint64_t)aw, R.jlo, R.jhi);
         R.bitmap_out[aw - R.w0] = win[i] & v;
       }
     } else {
-      // ---- 3. word-parallel Algorithm 2 --------------------------------
-      const uint32_t kwin = g.kwin, rec_t = g.rec_t;
-      const uint32_t kneed = min(rec_t, kwin + 1u);
-      uint32_t need = (kneed >= 32u) ? 0xFFFFFFFEu : (((1u << kneed) - 1u) & ~1u);
-      uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
-      for (uint32_t ib = g.mw + warp * 32u; ib < nwords; ib += nwarps * 32u) {
-        const uint32_t i = ib + lane;
-        const bool act = i < nwords;
-        const uint32_t w = act ? win[i] : 0u;
-        const uint32_t wp = act ? win[i - 1] : 0u;
-        const uint64_t J0 = 32ull * (uint64_t)(wstart + (int64_t)i);
-        const uint32_t valid = act ? valid_mask(J0, R.jlo, R.jhi) : 0u;
-        uint32_t unres = valid;
-        uint32_t pl[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-        scan_step<1, PER_N>(__funnelshift_l(wp, w, 1), unres, c1, need, pl, J0, rec_t, sh, a);
-        if (__any_sync(0xFFFFFFFFu, unres)) {
-          scan_step<2, PER_N>(__funnelshift_l(wp, w, 2), unres, c2, need, pl, J0, rec_t, sh, a);
-          if (__any_sync(0xFFFFFFFFu, unres)) {
-            scan_step<3, PER_N>(__funnelshift_l(wp, w, 4), unres, c3, need, pl, J0, rec_t, sh, a);
-            if (__any_sync(0xFFFFFFFFu, unres)) {
-              scan_step<4, PER_N>(__funnelshift_l(wp, w, 8), unres, c4, need, pl, J0, rec_t, sh, a);
-              if (__any_sync(0xFFFFFFFFu, unres)) {
-                scan_step<5, PER_N>(__funnelshift_l(wp, w, 16), unres, c5, need, pl, J0, rec_t, sh, a);
-                for (uint32_t k = 6; k <= kwin && __any_sync(0xFFFFFFFFu, unres); ++k) {
-                  const uint32_t sf = act ? win[i - (1u << (k - 6))] : 0u;
-                  const uint32_t hit = unres & sf;
-                  unres &= ~sf;
-                  if (PER_N) {
-#pragma unroll
-                    for (int j = 0; j < 6; ++j)
-                      if ((k >> j) & 1u) pl[j] |= hit;
-                  }
-                  if (hit) {
-                    atomicAdd(&sh.hist[k], (unsigned long long)__popc(hit));
-                    if (need & (1u << k)) {
-                      need &= ~(1u << k);
-                      atomicMin(&sh.first[k],
-                                (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(hit) - 1)) + 1ull));
-                    }
-                    if (k >= rec_t) list_append(a, R, hit, J0, k);
-                  }
-                }
-                if (unres) straggler_push(a, unres, J0, kwin + 1u, sh.req_idx);
-              }
-            }
-          }
-        }
-        if (PER_N && R.per_n_k) write_per_n(R.per_n_k, J0, R.jlo, valid, pl);
-      }
-      // warp totals of k = 1..5 into the tile histogram
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        c1 += __shfl_xor_sync(0xFFFFFFFFu, c1, o);
-        c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
-        c3 += __shfl_xor_sync(0xFFFFFFFFu, c3, o);
-        c4 += __shfl_xor_sync(0xFFFFFFFFu, c4, o);
-        c5 += __shfl_xor_sync(0xFFFFFFFFu, c5, o);
-      }
-      if (lane == 0) {
-        if (c1) atomicAdd(&sh.hist[1], (unsigned long long)c1);
-        if (c2) atomicAdd(&sh.hist[2], (unsigned long long)c2);
-        if (c3) atomicAdd(&sh.hist[3], (unsigned long long)c3);
-        if (c4) atomicAdd(&sh.hist[4], (unsigned long long)c4);
-        if (c5) atomicAdd(&sh.hist[5], (unsigned long long)c5);
-      }
+      // ---- 3. word-parallel Algorithm 2 ------------------------------------
+      // core words whose 32 bits are all valid: window indices [ifl, ifl+nfull)
+      const int64_t full_lo = (int64_t)((R.jlo + 31) >> 5) - wstart;
+      const int64_t full_hi = (int64_t)(R.jhi >> 5) - wstart;
+      const int64_t fl = max(full_lo, (int64_t)g.mw), fh = min(full_hi, (int64_t)nwords);
+      const uint32_t ifl = (uint32_t)fl;
+      const uint32_t nfull = fh > fl ? (uint32_t)(fh - fl) : 0u;
+      if (LEAN)
+        scan_tile_lean(win, a, sh, wstart, nwords, ifl, nfull);
+      else
+        scan_tile<LEAN, PER_N>(win, a, sh, wstart, nwords, ifl, nfull);
     }
+    if (tid == 0) sh.next_tile = next;
     __syncthreads();
+    if (LEAN) {
+      // words that were still unresolved after k = 5
+      const uint32_t nq = min(sh.defer_n, kDeferCap);
+      for (uint32_t e = tid; e < nq; e += S) {
+        const uint32_t i = sh.defer_i[e];
+        finish_word(win, i, sh.defer_u[e], wstart + (int64_t)i, a, sh);
+      }
+      __syncthreads();
+    }
 
-    // ---- 4. tile aggregates into the range's slot ------------------------
-    if (tid < kMaxK) {
+    // ---- 4. tile aggregates into the range's slot (warp 0) ------------------
+    if (warp == 0) {
+      unsigned long long h0 = sh.hist[lane], h1 = sh.hist[lane + 32];
+      if (LEAN && !R.sieve_only) {
+        // k = 1 was not counted: every other valid n of the tile is accounted for
+        unsigned long long rest = (lane >= 2 ? h0 : 0ull) + h1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xFFFFFFFFu, rest, o);
+        rest += sh.n_strag;
+        const unsigned long long jl = max((unsigned long long)R.jlo, 32ull * (unsigned long long)tws);
+        const unsigned long long jh = min((unsigned long long)R.jhi, 32ull * (unsigned long long)twe);
+        if (lane == 1) h0 = (jh > jl ? jh - jl : 0ull) - rest;
+      }
       ResultSlot *slot = &a.slots[R.slot];
-      const unsigned long long h = sh.hist[tid], f = sh.first[tid];
-      if (h) atomicAdd(&slot->hist[tid], h);
-      if (f != kNoN) atomicMin(&slot->first_n[tid], f);
-      sh.hist[tid] = 0ull;
-      sh.first[tid] = kNoN;
+      const unsigned long long f0 = sh.first[lane], f1 = sh.first[lane + 32];
+      if (h0) atomicAdd(&slot->hist[lane], h0);
+      if (h1) atomicAdd(&slot->hist[lane + 32], h1);
+      if (f0 != kNoN) atomicMin(&slot->first_n[lane], f0);
+      if (f1 != kNoN) atomicMin(&slot->first_n[lane + 32], f1);
+      sh.hist[lane] = 0ull;
+      sh.hist[lane + 32] = 0ull;
+      sh.first[lane] = kNoN;
+      sh.first[lane + 32] = kNoN;
+      __syncwarp();
+      if (lane == 0) {
+        sh.n_strag = 0;
+        sh.defer_n = 0;
+      }
+      __syncwarp();
     }
-    __syncthreads();
   }
 }
 
+// The stamped-prime counts instantiated (sv_config.stamp_primes).
+#define SV_FOR_EACH_NS(X) X(2) X(4) X(6) X(8)
+
+static int g_max_dyn_smem = 0;
+
 cudaError_t tile_kernel_setup(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  // The attribute is per kernel and process wide: raise it once to the
+  // largest window any configuration may use (the opt-in limit minus the
+  // static shared memory), so contexts with different tiles never disagree.
+  (void)smem;
+  if (g_max_dyn_smem) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+  const int max_dyn = optin - (int)sizeof(ScanShared) - 1024;
+#define SV_SET(NS)                                                                                    \
+  if ((e = cudaFuncSetAttribute(tile_kernel<0, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) || \
+      (e = cudaFuncSetAttribute(tile_kernel<1, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) || \
+      (e = cudaFuncSetAttribute(tile_kernel<2, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)))   \
+    return e;
+  SV_FOR_EACH_NS(SV_SET)
+#undef SV_SET
+  g_max_dyn_smem = max_dyn;
+  return cudaSuccess;
 }
 
-cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem, bool per_n,
-                         cudaStream_t st) {
+size_t tile_static_smem() { return sizeof(ScanShared); }
+
+cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem, int mode, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  if (per_n)
-    tile_kernel<true><<<grid, threads, smem, st>>>(a);
-  else
-    tile_kernel<false><<<grid, threads, smem, st>>>(a);
-  return cudaGetLastError();
+  const int ns = (int)a.g.i_med;
+#define SV_LAUNCH(NS)                                                          \
+  if (ns == NS) {                                                              \
+    if (mode == 2) tile_kernel<2, NS><<<grid, threads, smem, st>>>(a);         \
+    else if (mode == 1) tile_kernel<1, NS><<<grid, threads, smem, st>>>(a);    \
+    else tile_kernel<0, NS><<<grid, threads, smem, st>>>(a);                   \
+    return cudaGetLastError();                                                 \
+  }
+  SV_FOR_EACH_NS(SV_LAUNCH)
+#undef SV_LAUNCH
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace sv

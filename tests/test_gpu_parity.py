@@ -92,6 +92,9 @@ KNOBS = [
     dict(tile_log2=18, threads=512, ctas_per_sm=2),
     dict(tile_log2=20, margin_log2=18),
     dict(tile_log2=15, record_k_threshold=3),   # long lists
+    dict(stamp_primes=2),
+    dict(stamp_primes=6, tile_log2=19, threads=512, ctas_per_sm=2, margin_log2=13),
+    dict(stamp_primes=8, tile_log2=16, record_k_threshold=5),
 ]
 
 
