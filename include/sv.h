@@ -247,6 +247,41 @@ sv_status sv_set_config(sv_ctx *ctx, const sv_config *cfg);
  * (inputs, descriptors, aggregates, lists, per-n values). */
 sv_status sv_last_transfer(const sv_ctx *ctx, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
 
+/*
+ * sv_verify_range for callers that cannot allocate memory when they verify:
+ * code running while a CUDA graph is captured (cudaMalloc is not allowed
+ * then), real-time loops that must not reach the allocator, processes whose
+ * memory budget is fixed at start-up.  The paper has no counterpart: this is
+ * a property of this library's interface, not of the method.
+ *
+ * It computes exactly what sv_verify_range computes, with the same kernels,
+ * and allocates nothing: no cudaMalloc, cudaFree or cudaMallocHost and no
+ * other allocating routine.  All scratch memory (launch header, descriptor,
+ * result slot, tile buckets, straggler queue, list and failure arenas) comes
+ * from one fixed 8 MiB array in device memory that the library declares at
+ * file scope; every GPU that loads the library holds those 8 MiB until the
+ * process exits.  Results are written into the caller's buffers in *out
+ * (HOST memory, as for sv_verify_range).
+ *
+ * Limits and rules:
+ *   - hi - lo <= 2^32, and the range's tile buckets must fit the array (true
+ *     for every such range with the default tile size); otherwise SV_ERANGE.
+ *   - At most 65536 listed n (mink >= T) and 1024 failures per call; more
+ *     listed n gives SV_EOVERFLOW.  out->per_n_k must be NULL (SV_EINVAL).
+ *   - sv_init_primes must have been called before (it allocates, once, at
+ *     set-up): SV_ENOPRIMES otherwise.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture begins.
+ *   - Every call shares the one array, which keeps the previous call's
+ *     contents (the call clears what must start at zero).  Calls that overlap
+ *     on the GPU -- from different contexts or threads on the same device --
+ *     race on it and must not be issued; calls through one context are
+ *     serialised by the context.
+ * Errors: SV_EINVAL, SV_ERANGE, SV_ENOPRIMES, SV_ECUDA, SV_EOVERFLOW.
+ */
+sv_status sv_verify_range_noalloc(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_range_result *out);
+
 /* Number of kernels this context has launched so far. */
 uint64_t sv_kernel_launches(const sv_ctx *ctx);
 

@@ -60,6 +60,7 @@ _SIGS = {
     "sv_init_primes": (ctypes.c_int, [_CTX, u64]),
     "sv_prime_count": (ctypes.c_int, [_CTX, P(u64), P(u64)]),
     "sv_verify_range": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
+    "sv_verify_range_noalloc": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
     "sv_verify_batch": (ctypes.c_int, [_CTX, P(u64), P(u64), ctypes.c_size_t, P(sv_range_result)]),
     "sv_min_k": (ctypes.c_int, [_CTX, P(u64), ctypes.c_size_t, P(u8)]),
     "sv_min_k_device": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -156,6 +157,10 @@ def sv_prime_count(ctx) -> tuple[int, int]:
 
 def sv_verify_range(ctx, lo: int, hi: int, out: sv_range_result) -> int:
     return load().sv_verify_range(ctx, lo, hi, ctypes.byref(out))
+
+
+def sv_verify_range_noalloc(ctx, lo: int, hi: int, out: sv_range_result) -> int:
+    return load().sv_verify_range_noalloc(ctx, lo, hi, ctypes.byref(out))
 
 
 def sv_verify_batch(ctx, lo: np.ndarray, hi: np.ndarray, out) -> int:

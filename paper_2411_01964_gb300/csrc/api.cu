@@ -441,6 +441,12 @@ sv_status check_range(const sv_ctx *c, uint64_t lo, uint64_t hi) {
 
 namespace sv {
 
+// Accessors for the no-allocation entry point (noalloc.cu); none allocates.
+Geometry geometry_for_span(const sv_ctx *c, uint64_t span_bits) { return make_geometry(c, span_bits); }
+PrimeTab prime_table_of(const sv_ctx *c) { return prime_tab(c); }
+uint32_t primes_upto_of(const sv_ctx *c, uint64_t x) { return primes_upto(c, x); }
+sv_status tile_smem_ready(sv_ctx *c) { return ensure_tile_smem(c); }
+
 // Runs a launch of ranges to completion, growing buffers and repeating the
 // launch when the device reports an overflow.  Results never depend on the
 // buffer sizes.

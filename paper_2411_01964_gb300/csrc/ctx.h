@@ -142,6 +142,10 @@ sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_rang
 sv_status launch_points_async(sv_ctx *c, uint64_t count, Workspace &ws, cudaStream_t st);
 uint64_t host_isqrt(uint64_t x);
 uint64_t range_odd_count(uint64_t lo, uint64_t hi);
+Geometry geometry_for_span(const sv_ctx *c, uint64_t span_bits);
+PrimeTab prime_table_of(const sv_ctx *c);
+uint32_t primes_upto_of(const sv_ctx *c, uint64_t x);
+sv_status tile_smem_ready(sv_ctx *c);
 Server *server_create(sv_ctx *c);
 void server_destroy(Server *s);
 sv_status server_submit(Server *s, const sv_request *req, uint64_t *ticket);
