@@ -151,6 +151,85 @@ def measured_traffic(n_odd: int):
     return t["dram_bytes_per_odd_n"] * n_odd
 
 
+def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3) -> dict:
+    """Config 4: 4096 ranges (seed 7) as one batched graph launch, against the
+    plain path (one range per launch, back to back on the same stream)."""
+    import torch
+    from paper_2411_01964_gb300 import Verifier
+    c = v0.config
+    v = Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream, tile_log2=c.tile_log2, threads=c.threads,
+                 ctas_per_sm=c.ctas_per_sm, margin_log2=c.margin_log2, stamp_primes=c.stamp_primes)
+    reqs = inputs.batch_requests(7, n_requests)
+    los = [a for a, _ in reqs]
+    his = [b for _, b in reqs]
+    n_odd = sum(odd_count(a, b) for a, b in reqs)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    v.launch_batch(los, his)  # warm-up: captures the graph
+    first = v.fetch_batch(list_cap=16)
+    bt = []
+    for _ in range(reps):
+        flush.zero_()
+        ev[0].record(stream)
+        v.launch_batch(los, his)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        bt.append(ev[0].elapsed_time(ev[1]))
+        res = v.fetch_batch(list_cap=16)
+    assert [r.hist for r in res] == [r.hist for r in first]
+    # plain path: one launch per range
+    flush.zero_()
+    ev[0].record(stream)
+    for a, b in reqs:
+        v.launch_range(a, b)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    pt = ev[0].elapsed_time(ev[1])
+    last = v.fetch_range(list_cap=16)
+    assert last.hist == res[-1].hist, "plain and batched paths disagree"
+    ms = sum(bt) / len(bt)
+    v.close()
+    return {"workload": f"{n_requests} ranges, seed 7 (starts odd in [2^30, 2^50), lengths 2^10..2^28)",
+            "odd_n": n_odd, "ms": ms, "value": n_odd / (ms / 1e3), "unit": UNIT,
+            "plain_ms": pt, "plain_value": n_odd / (pt / 1e3),
+            "speedup_vs_plain": pt / ms, "graph": "one captured graph, replayed per batch"}
+
+
+def bench_serving(stream, seconds: float, batched: dict | None) -> dict:
+    """Config 5: Poisson arrivals (seed 11) of the serving mix at several
+    rates; latency from submission to completion, throughput over the run."""
+    from paper_2411_01964_gb300 import Verifier, B
+    out = []
+    for rate in (1e2, 1e3, 1e4, 1e5):
+        count = int(min(2000, max(60, rate * seconds)))
+        reqs = inputs.serving_requests(rate, count)
+        odd = sum(odd_count(r.lo, r.hi) if r.kind != "points" else len(r.points) for r in reqs)
+        with Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream) as sv:
+            sv.min_k([3])  # context ready; the server thread starts on the first submit
+            tickets = []
+            t0 = time.perf_counter()
+            for r in reqs:
+                dt = t0 + r.t_arrival - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                if r.kind == "points":
+                    tickets.append(sv.submit_points(r.points))
+                else:
+                    tickets.append(sv.submit_range(r.lo, r.hi, list_cap=64))
+            for t in tickets:
+                st = sv.poll(t, -1)
+                assert st == B.SV_OK, B.sv_strerror(st)
+            t1 = time.perf_counter()
+            s = sv.server_stats()
+            out.append({"rate_per_s": rate, "requests": count, "odd_n": odd,
+                        "value": odd / (t1 - t0), "unit": UNIT,
+                        "offered": odd / max(reqs[-1].t_arrival, 1e-9),
+                        "p50_us": s.p50_us, "p99_us": s.p99_us, "launches": s.launches})
+    best = max(o["value"] for o in out)
+    return {"workload": "Poisson arrivals, seed 11: 70% ranges 2^12..2^16, 20% ranges 2^24..2^30, "
+                        "10% batches of 1..1024 points in [3, 2^50)",
+            "rates": out, "best_value": best, "unit": UNIT}
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -232,6 +311,10 @@ def main() -> int:
     ap.add_argument("--stamp-primes", type=int, default=0)
     ap.add_argument("--range", default="", help="LO:HI overrides the workload's range (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-requests", type=int, default=4096)
+    ap.add_argument("--serve-seconds", type=float, default=1.5)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -364,6 +447,10 @@ def main() -> int:
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lo, hi, args.cpu_seconds, 1 << 34)
+    if rank == 0 and world == 1 and not args.no_batch:
+        line["batched"] = bench_batch(v, stream, flush, args.batch_requests)
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["served"] = bench_serving(stream, args.serve_seconds, line.get("batched"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -204,6 +204,16 @@ sv_status sv_launch_range(sv_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *d_per_
  * buffer given to sv_launch_range). */
 sv_status sv_fetch_range(sv_ctx *ctx, sv_range_result *out);
 
+/*
+ * Device-resident form of sv_verify_batch: enqueue the batch as one replay of
+ * the captured launch graph and return without waiting (list capacity per
+ * range: sv_config.list_capacity).  sv_fetch_batch waits and copies the
+ * aggregates into out[0..count) (count must match).  One launch may be
+ * pending per context (a range or a batch).
+ */
+sv_status sv_launch_batch(sv_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t count);
+sv_status sv_fetch_batch(sv_ctx *ctx, sv_range_result *out, size_t count);
+
 /* Device-resident form of sv_min_k: d_points / d_out_k are DEVICE arrays;
  * enqueued on the context's stream, no wait. */
 sv_status sv_min_k_device(sv_ctx *ctx, const uint64_t *d_points, size_t count, uint8_t *d_out_k);

@@ -177,6 +177,24 @@ class Verifier:
         B.check(B.sv_fetch_range(self.ctx, buf.res), "sv_fetch_range")
         return buf.result()
 
+    def launch_batch(self, los, his) -> None:
+        self._pending_batch = len(los)
+        B.check(B.sv_launch_batch(self.ctx, np.asarray(los, dtype=np.uint64), np.asarray(his, dtype=np.uint64)),
+                "sv_launch_batch")
+
+    def fetch_batch(self, *, list_cap: int = 1 << 12, fail_cap: int = 16) -> list:
+        n = self._pending_batch
+        bufs = [_ResultBuffers(list_cap, fail_cap, None) for _ in range(n)]
+        arr = (B.sv_range_result * max(n, 1))()
+        for i, b in enumerate(bufs):
+            arr[i] = b.res
+        B.check(B.sv_fetch_batch(self.ctx, arr, n), "sv_fetch_batch")
+        out = []
+        for i, b in enumerate(bufs):
+            b.res = arr[i]
+            out.append(b.result())
+        return out
+
     def min_k_device(self, d_points, d_out) -> None:
         B.check(B.sv_min_k_device(self.ctx, d_points.data_ptr(), d_points.numel(), d_out.data_ptr()),
                 "sv_min_k_device")

@@ -62,6 +62,8 @@ _SIGS = {
     "sv_verify_range": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
     "sv_verify_range_noalloc": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
     "sv_verify_batch": (ctypes.c_int, [_CTX, P(u64), P(u64), ctypes.c_size_t, P(sv_range_result)]),
+    "sv_launch_batch": (ctypes.c_int, [_CTX, P(u64), P(u64), ctypes.c_size_t]),
+    "sv_fetch_batch": (ctypes.c_int, [_CTX, P(sv_range_result), ctypes.c_size_t]),
     "sv_min_k": (ctypes.c_int, [_CTX, P(u64), ctypes.c_size_t, P(u8)]),
     "sv_min_k_device": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "sv_sieve_bitmap": (ctypes.c_int, [_CTX, u64, u64, ctypes.c_void_p]),
@@ -167,6 +169,16 @@ def sv_verify_batch(ctx, lo: np.ndarray, hi: np.ndarray, out) -> int:
     lo = np.ascontiguousarray(lo, dtype=np.uint64)
     hi = np.ascontiguousarray(hi, dtype=np.uint64)
     return load().sv_verify_batch(ctx, lo.ctypes.data_as(P(u64)), hi.ctypes.data_as(P(u64)), len(lo), out)
+
+
+def sv_launch_batch(ctx, lo: np.ndarray, hi: np.ndarray) -> int:
+    lo = np.ascontiguousarray(lo, dtype=np.uint64)
+    hi = np.ascontiguousarray(hi, dtype=np.uint64)
+    return load().sv_launch_batch(ctx, lo.ctypes.data_as(P(u64)), hi.ctypes.data_as(P(u64)), len(lo))
+
+
+def sv_fetch_batch(ctx, out, count: int) -> int:
+    return load().sv_fetch_batch(ctx, out, count)
 
 
 def sv_min_k(ctx, points: np.ndarray, out_k: np.ndarray) -> int:

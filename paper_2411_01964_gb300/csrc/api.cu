@@ -18,6 +18,10 @@ using namespace sv;
 namespace sv {
 
 void Workspace::release_all() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  gexec = nullptr;
+  if (staged) cudaEventDestroy(staged);
+  staged = nullptr;
   reqs.release();
   h_reqs.release();
   hdr.release();
@@ -136,8 +140,7 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   g.i_large = il;
   // expected bucket hits per full window: 32*(tw+mw) * sum_{large p} 1/p^2
   // (only sizes a buffer; overflow is detected and the launch repeated)
-  double s = 0.0;
-  for (uint32_t j = il; j < c->n_primes; ++j) s += 1.0 / ((double)c->h_p[j] * (double)c->h_p[j]);
+  const double s = il < c->inv_sq_suffix.size() ? c->inv_sq_suffix[il] : 0.0;  // sum_{j >= il} 1/p_j^2
   const double lam = 32.0 * (double)(g.tw + g.mw) * s;
   uint32_t cap = (uint32_t)(lam + 8.0 * std::sqrt(lam) + 64.0);
   cap = (cap + 31u) & ~31u;
@@ -170,6 +173,8 @@ sv_status ensure_tile_smem(sv_ctx *c) {
 // Plans the descriptors of `specs` into ws.h_reqs / ws.h_hdr.
 sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g, Workspace &ws) {
   const uint32_t n = (uint32_t)specs.size();
+  // the previous launch may still be copying from the pinned staging
+  if (ws.staged && cudaEventSynchronize(ws.staged) != cudaSuccess) return SV_ECUDA;
   if (ws.h_reqs.ensure(n ? n : 1) != cudaSuccess) return SV_ENOMEM;
   if (ws.h_hdr.ensure(1) != cudaSuccess) return SV_ENOMEM;
   uint64_t tiles = 0, list_total = 0, fail_total = 0;
@@ -274,6 +279,8 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
   SV_TRY_CUDA(cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, st));
   SV_TRY_CUDA(cudaMemcpyAsync(ws.hdr.p, ws.h_hdr.p, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st));
   ws.h2d_bytes = sizeof(ReqDesc) * n + sizeof(LaunchHeader);
+  if (!ws.staged && cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming) != cudaSuccess) return SV_ECUDA;
+  SV_TRY_CUDA(cudaEventRecord(ws.staged, st));
   {
     KTimer kt(c, kKInit, st);
     SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, ws.total_tiles, st));
@@ -336,6 +343,105 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     }
     c->launches++;
   }
+  return SV_OK;
+}
+
+// The same launch as a CUDA graph.  The grids are fixed and persistent (every
+// kernel reads the launch's sizes from the device header), so one captured
+// graph is replayed for every launch that fits the current buffers, geometry
+// and kernel mode; it is re-captured when any of them changes.
+sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) {
+  const uint32_t n = ws.n_reqs;
+  if (ws.reqs.ensure(n ? n : 1) || ws.hdr.ensure(1) || ws.slots.ensure(n ? n : 1) ||
+      ws.h_slots.ensure(n ? n : 1) || ws.list_n.ensure(ws.list_total ? ws.list_total : 1) ||
+      ws.list_k.ensure(ws.list_total ? ws.list_total : 1) || ws.fail_n.ensure(ws.fail_total ? ws.fail_total : 1) ||
+      ws.strag.ensure(ws.strag_cap) || ws.bucket_count.ensure(ws.total_tiles ? ws.total_tiles : 1) ||
+      ws.bucket_data.ensure((size_t)(ws.total_tiles ? ws.total_tiles : 1) * g.bucket_cap))
+    return SV_ENOMEM;
+  ws.bucket_cap = g.bucket_cap;
+  const int mode = ws.any_per_n ? 2 : (g.rec_t <= 5 ? 1 : 0);
+  const size_t req_copy = std::min(ws.h_reqs.cap, ws.reqs.cap);
+  GraphKey key;
+  std::memset(&key, 0, sizeof(key));
+  const void *ptrs[] = {ws.reqs.p,    ws.hdr.p,   ws.slots.p,        ws.list_n.p,       ws.list_k.p,
+                        ws.fail_n.p,  ws.strag.p, ws.bucket_count.p, ws.bucket_data.p, ws.h_reqs.p,
+                        ws.h_hdr.p,   c->d_p,     (const void *)st};
+  std::memcpy(key.p, ptrs, sizeof(ptrs));
+  key.g = g;
+  key.threads = c->cfg.threads;
+  key.ctas = c->cfg.ctas_per_sm;
+  key.mode = (uint32_t)mode;
+  key.strag_cap = ws.strag_cap;
+  key.req_copy = req_copy;
+  key.n_table = c->n_primes;
+  if (!ws.gexec || std::memcmp(&key, &ws.gkey, sizeof(key)) != 0) {
+    if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
+    ws.gexec = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SV_ECUDA;
+    const PrimeTab pt = prime_tab(c);
+    cudaError_t e = cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * req_copy, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(ws.hdr.p, ws.h_hdr.p, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st);
+    if (!e) e = launch_init(ws.hdr.p, ws.slots.p, 1u << 20, ws.bucket_count.p, 1u << 20, st);
+    if (!e && pt.n > g.i_large) {
+      BucketArgs b{};
+      b.pt = pt;
+      b.g = g;
+      b.reqs = ws.reqs.p;
+      b.hdr = ws.hdr.p;
+      b.bucket_count = ws.bucket_count.p;
+      b.bucket_data = ws.bucket_data.p;
+      e = launch_bucket_fill(b, pt.n - g.i_large, 1u << 20, st);
+    }
+    if (!e) {
+      TileArgs t{};
+      t.pt = pt;
+      t.g = g;
+      t.reqs = ws.reqs.p;
+      t.hdr = ws.hdr.p;
+      t.slots = ws.slots.p;
+      t.list_n = ws.list_n.p;
+      t.list_k = ws.list_k.p;
+      t.fail_n = ws.fail_n.p;
+      t.strag = ws.strag.p;
+      t.strag_cap = ws.strag_cap;
+      t.bucket_count = ws.bucket_count.p;
+      t.bucket_data = ws.bucket_data.p;
+      e = launch_tiles(t, c->cfg.threads, (uint32_t)c->num_sms * c->cfg.ctas_per_sm, 4ull * (g.tw + g.mw), mode, st);
+    }
+    if (!e) {
+      StragArgs sa{};
+      sa.pt = pt;
+      sa.reqs = ws.reqs.p;
+      sa.hdr = ws.hdr.p;
+      sa.slots = ws.slots.p;
+      sa.list_n = ws.list_n.p;
+      sa.list_k = ws.list_k.p;
+      sa.fail_n = ws.fail_n.p;
+      sa.strag = ws.strag.p;
+      sa.strag_cap = ws.strag_cap;
+      sa.rec_t = g.rec_t;
+      e = launch_stragglers(sa, (uint32_t)c->num_sms * 2, st);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    if (e || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return SV_ECUDA;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&ws.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+      ws.gexec = nullptr;
+      return SV_ECUDA;
+    }
+    ws.gkey = key;
+  }
+  SV_TRY_CUDA(cudaGraphLaunch(ws.gexec, st));
+  // the graph reads the staging when it runs: the next plan waits for it
+  if (!ws.staged && cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming) != cudaSuccess) return SV_ECUDA;
+  SV_TRY_CUDA(cudaEventRecord(ws.staged, st));
+  c->launches += 4;
+  ws.h2d_bytes = sizeof(ReqDesc) * req_copy + sizeof(LaunchHeader);
   return SV_OK;
 }
 
@@ -441,6 +547,17 @@ sv_status check_range(const sv_ctx *c, uint64_t lo, uint64_t hi) {
 
 namespace sv {
 
+// 1 - c_l from Table 2 (Sec. 2): the heuristic probability that mink > l.
+// Only sizes buffers; results never depend on it.
+constexpr double kTail[8] = {1.0, 1.8943e-1, 2.4129e-2, 2.1482e-3, 1.3902e-4, 6.8527e-6, 2.6694e-7, 4.9973e-8};
+
+uint64_t list_cap_estimate(uint64_t n_odd, uint32_t T, uint64_t cap) {
+  if (cap == 0) return 0;
+  const double p = T < 8 ? kTail[T ? T - 1 : 0] : kTail[7];
+  const uint64_t est = (uint64_t)(2.0 * p * (double)n_odd) + 256;
+  return std::min<uint64_t>(est, cap);
+}
+
 // Accessors for the no-allocation entry point (noalloc.cu); none allocates.
 Geometry geometry_for_span(const sv_ctx *c, uint64_t span_bits) { return make_geometry(c, span_bits); }
 PrimeTab prime_table_of(const sv_ctx *c) { return prime_tab(c); }
@@ -451,14 +568,14 @@ sv_status tile_smem_ready(sv_ctx *c) { return ensure_tile_smem(c); }
 // launch when the device reports an overflow.  Results never depend on the
 // buffer sizes.
 sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result **outs, cudaStream_t st,
-                     Workspace &ws) {
+                     Workspace &ws, bool graph) {
   sv_status s = ensure_tile_smem(c);
   if (s) return s;
   Geometry g = make_geometry(c, max_span_bits(c, specs));
   if (ws.bucket_cap > g.bucket_cap) g.bucket_cap = ws.bucket_cap;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if ((s = plan(c, specs, g, ws))) return s;
-    if ((s = enqueue(c, g, ws, st))) return s;
+    if ((s = graph ? enqueue_graph(c, g, ws, st) : enqueue(c, g, ws, st))) return s;
     Collect what;
     if ((s = collect(c, specs, outs, ws, st, &what))) return s;
     if (what == kDone) {
@@ -487,7 +604,7 @@ sv_status launch_ranges_async(sv_ctx *c, std::vector<RangeSpec> &specs, Workspac
   Geometry g = make_geometry(c, max_span_bits(c, specs));
   if (ws.bucket_cap > g.bucket_cap) g.bucket_cap = ws.bucket_cap;
   if ((s = plan(c, specs, g, ws))) return s;
-  return enqueue(c, g, ws, st);
+  return enqueue_graph(c, g, ws, st);
 }
 
 sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_result **outs, Workspace &ws,
@@ -659,6 +776,10 @@ sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
   c->n_primes = n;
   c->n_div = n_div;
   c->h_p.swap(hp);
+  // suffix sums of 1/p^2 (sizing of the tile buckets, host only)
+  c->inv_sq_suffix.assign(c->h_p.size() + 1, 0.0);
+  for (size_t j = c->h_p.size(); j-- > 0;)
+    c->inv_sq_suffix[j] = c->inv_sq_suffix[j + 1] + 1.0 / ((double)c->h_p[j] * (double)c->h_p[j]);
   c->pmax = pmax;
   c->max_hi = max_hi;
   c->launches += 5;
@@ -695,7 +816,7 @@ sv_status sv_verify_range(sv_ctx *c, uint64_t lo, uint64_t hi, sv_range_result *
     specs[0].d_per_n = c->ws.per_n.p;
   }
   sv_range_result *outs[1] = {out};
-  s = run_ranges(c, specs, outs, c->stream, c->ws);
+  s = run_ranges(c, specs, outs, c->stream, c->ws, false);
   if (s) return s;
   if (out->per_n_k && n_odd) {
     if (cudaMemcpyAsync(out->per_n_k, c->ws.per_n.p, n_odd, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -723,7 +844,52 @@ sv_status sv_verify_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, siz
     outs[i] = &out[i];
   }
   if (count == 0) return SV_OK;
-  return run_ranges(c, specs, outs.data(), c->stream, c->ws);
+  return run_ranges(c, specs, outs.data(), c->stream, c->ws, true);
+}
+
+sv_status sv_launch_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t count) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (count == 0 || !lo || !hi) return SV_EINVAL;
+  for (size_t i = 0; i < count; ++i)
+    if ((s = check_range(c, lo[i], hi[i]))) return s;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((s = ensure_tile_smem(c))) return s;
+  std::vector<RangeSpec> specs(count);
+  for (size_t i = 0; i < count; ++i) {
+    specs[i].lo = lo[i];
+    specs[i].hi = hi[i];
+    specs[i].list_cap = list_cap_estimate(range_odd_count(lo[i], hi[i]), c->cfg.record_k_threshold,
+                                          c->cfg.list_capacity);
+    specs[i].fail_cap = 16;
+  }
+  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
+  if ((s = plan(c, specs, g, c->ws))) return s;
+  if ((s = enqueue_graph(c, g, c->ws, c->stream))) return s;
+  c->pending = true;
+  c->pending_graph = true;
+  c->pending_specs.swap(specs);
+  return SV_OK;
+}
+
+sv_status sv_fetch_batch(sv_ctx *c, sv_range_result *out, size_t count) {
+  if (!c || (count && !out)) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!c->pending || count != c->pending_specs.size()) return SV_EINVAL;
+  c->pending = false;
+  std::vector<sv_range_result *> outs(count);
+  for (size_t i = 0; i < count; ++i) outs[i] = &out[i];
+  Collect what;
+  sv_status s = collect(c, c->pending_specs, outs.data(), c->ws, c->stream, &what);
+  if (s) return s;
+  if (what != kDone) {
+    std::vector<RangeSpec> specs = c->pending_specs;
+    if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
+    if (what == kRetryStrag) c->ws.strag_cap *= 4;
+    s = run_ranges(c, specs, outs.data(), c->stream, c->ws, true);
+  }
+  return s;
 }
 
 sv_status sv_min_k(sv_ctx *c, const uint64_t *points, size_t count, uint8_t *out_k) {
@@ -761,7 +927,7 @@ sv_status sv_sieve_bitmap(sv_ctx *c, uint64_t lo, uint64_t hi, uint32_t *d_bitma
   specs[0].hi = hi;
   specs[0].sieve_only = true;
   specs[0].bitmap_out = d_bitmap;
-  return run_ranges(c, specs, nullptr, c->stream, c->ws);
+  return run_ranges(c, specs, nullptr, c->stream, c->ws, false);
 }
 
 sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_k) {
@@ -788,7 +954,7 @@ sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_
 sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
   if (!c || !out) return SV_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
-  if (!c->pending) return SV_EINVAL;
+  if (!c->pending || c->pending_specs.size() != 1) return SV_EINVAL;
   c->pending = false;
   sv_range_result *outs[1] = {out};
   Collect what;
@@ -799,7 +965,7 @@ sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
     std::vector<RangeSpec> specs = c->pending_specs;
     if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
     if (what == kRetryStrag) c->ws.strag_cap *= 4;
-    s = run_ranges(c, specs, outs, c->stream, c->ws);
+    s = run_ranges(c, specs, outs, c->stream, c->ws, false);
     if (s) return s;
   }
   c->last_h2d = c->ws.h2d_bytes;
@@ -913,7 +1079,7 @@ sv_status sv_autotune(sv_ctx *c, uint64_t lo, uint64_t hi, sv_config *chosen) {
               specs[0].hi = hi;
               specs[0].fail_cap = 16;
               const auto t0 = std::chrono::steady_clock::now();
-              s = run_ranges(c, specs, outs, c->stream, c->ws);
+              s = run_ranges(c, specs, outs, c->stream, c->ws, false);
               const auto t1 = std::chrono::steady_clock::now();
               if (s) break;
               const double dt = std::chrono::duration<double>(t1 - t0).count();

@@ -54,6 +54,15 @@ struct RangeSpec {
   uint32_t *bitmap_out = nullptr;
 };
 
+// What a captured launch graph depends on (compared bytewise).
+struct GraphKey {
+  const void *p[13];
+  Geometry g;
+  uint32_t threads, ctas, mode, strag_cap;
+  uint64_t req_copy;
+  uint32_t n_table, pad;
+};
+
 // Everything one launch needs on the device, reused across launches.
 struct Workspace {
   DBuf<ReqDesc> reqs;
@@ -83,6 +92,10 @@ struct Workspace {
   uint32_t bucket_cap = 0;
   bool any_per_n = false;
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
+  // the captured launch graph and what it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  GraphKey gkey{};
+  cudaEvent_t staged = nullptr;  // recorded after the launch's reads of the pinned staging
   void release_all();
 };
 
@@ -104,10 +117,12 @@ struct sv_ctx {
   uint64_t *d_mu = nullptr, *d_inv = nullptr, *d_lim = nullptr;
   uint32_t n_primes = 0, n_div = 0;
   std::vector<uint32_t> h_p;
+  std::vector<double> inv_sq_suffix;  // sum over j >= i of 1/p_j^2 (bucket sizing only)
   std::atomic<size_t> smem_set{0};  // dynamic smem the tile kernel was configured for
   sv::Workspace ws;
   // device-resident pending launch
   bool pending = false;
+  bool pending_graph = false;
   std::vector<sv::RangeSpec> pending_specs;
   // per-kernel timing with events on the launching stream (sv_kernel_timing)
   bool kprof = false;
@@ -128,7 +143,7 @@ struct sv_ctx {
 namespace sv {
 // Shared by api.cu and server.cu.
 sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result **outs, cudaStream_t st,
-                     Workspace &ws);
+                     Workspace &ws, bool graph = false);
 sv_status run_points(sv_ctx *c, const uint64_t *points, size_t count, uint8_t *out_k, cudaStream_t st,
                      Workspace &ws);
 // Asynchronous halves used by the serving loop: enqueue a launch of ranges on
@@ -142,6 +157,10 @@ sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_rang
 sv_status launch_points_async(sv_ctx *c, uint64_t count, Workspace &ws, cudaStream_t st);
 uint64_t host_isqrt(uint64_t x);
 uint64_t range_odd_count(uint64_t lo, uint64_t hi);
+// Device list entries to reserve for a range of n_odd odd n with threshold T
+// (twice the heuristic expectation plus slack, at most cap); an overflow is
+// detected on the device and the launch repeated with exact room.
+uint64_t list_cap_estimate(uint64_t n_odd, uint32_t T, uint64_t cap);
 Geometry geometry_for_span(const sv_ctx *c, uint64_t span_bits);
 PrimeTab prime_table_of(const sv_ctx *c);
 uint32_t primes_upto_of(const sv_ctx *c, uint64_t x);

@@ -38,10 +38,6 @@ constexpr uint64_t kMaxPointsPerLaunch = 1ull << 16;
 constexpr size_t kMaxChunksPerLaunch = 4096;
 constexpr size_t kMaxQueued = 1u << 20;
 
-// 1 - c_l from Table 2 (Sec. 2): probability that mink > l.  Only used to size
-// the device list of a chunk; an overflow is detected and the chunk repeated.
-constexpr double kTail[8] = {1.0, 1.8943e-1, 2.4129e-2, 2.1482e-3, 1.3902e-4, 6.8527e-6, 2.6694e-7, 4.9973e-8};
-
 struct Request {
   uint64_t ticket = 0;
   sv_request r{};
@@ -82,10 +78,7 @@ struct Slot {
 };
 
 uint64_t chunk_list_cap(uint64_t n_odd, uint32_t T, uint64_t caller_cap) {
-  if (caller_cap == 0) return 0;
-  const double p = T < 8 ? kTail[T ? T - 1 : 0] : kTail[7];
-  const uint64_t est = (uint64_t)(2.0 * p * (double)n_odd) + 256;
-  return std::min<uint64_t>(est, caller_cap);
+  return list_cap_estimate(n_odd, T, caller_cap);
 }
 
 }  // namespace

@@ -174,3 +174,25 @@ def test_repeatable(gpu):
     a = gpu.verify_range(lo, hi, per_n=True)
     b = gpu.verify_range(lo, hi, per_n=True)
     assert a.hist == b.hist and np.array_equal(a.per_n_k, b.per_n_k)
+
+
+def test_batch_graph_replay_and_recapture(orc):
+    """Consecutive batches replay one captured graph; a batch that needs larger
+    buffers re-captures it.  Every result equals the oracle's."""
+    with Verifier(max_hi=(1 << 50) + (1 << 28)) as v:
+        b1 = inputs.batch_requests(7, 40)
+        b1 = [(lo, lo + min(hi - lo, 1 << 20)) for lo, hi in b1]
+        b2 = inputs.batch_requests(8, 40)
+        b2 = [(lo, lo + min(hi - lo, 1 << 19)) for lo, hi in b2]
+        b3 = b2[:5] + [((1 << 44) + 1, (1 << 44) + 1 + (1 << 26))]  # more tiles: new buffers
+        for batch in (b1, b2, b1, b3):
+            res = v.verify_batch([a for a, _ in batch], [b for _, b in batch], list_cap=4096)
+            for (lo, hi), g in zip(batch, res):
+                o = orc.verify_range(lo, hi)
+                assert g.hist == o.hist and g.first_n == o.first_n
+                assert np.array_equal(g.list_n, o.list_n)
+        # device-resident form
+        v.launch_batch([a for a, _ in b2], [b for _, b in b2])
+        res = v.fetch_batch(list_cap=4096)
+        for (lo, hi), g in zip(b2, res):
+            assert g.hist == orc.verify_range(lo, hi).hist
