@@ -138,6 +138,11 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   if (il < g.i_dense) il = g.i_dense;
   if (il > g.i_dense + (uint32_t)kMaxSparsePrimes) il = g.i_dense + (uint32_t)kMaxSparsePrimes;
   g.i_large = il;
+  // primes >= 2^20 reach the buckets by enumerating multipliers (bucket_fill_j_kernel)
+  uint32_t ih = primes_upto(c, (1u << 20) - 1);
+  if (ih < il) ih = il;
+  g.i_hyb = ih;
+  g.p_hyb = ih < c->n_primes ? c->h_p[ih] : 0xFFFFFFFFu;
   // expected bucket hits per full window: 32*(tw+mw) * sum_{large p} 1/p^2
   // (only sizes a buffer; overflow is detected and the launch repeated)
   const double s = il < c->inv_sq_suffix.size() ? c->inv_sq_suffix[il] : 0.0;  // sum_{j >= il} 1/p_j^2
@@ -156,6 +161,8 @@ PrimeTab prime_tab(const sv_ctx *c) {
   pt.mu = c->d_mu;
   pt.inv = c->d_inv;
   pt.lim = c->d_lim;
+  pt.bits = c->d_pbits;
+  pt.bits_words = c->pbits_words;
   pt.n = c->n_primes;
   pt.n_div = c->n_div;
   return pt;
@@ -179,6 +186,8 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   if (ws.h_hdr.ensure(1) != cudaSuccess) return SV_ENOMEM;
   uint64_t tiles = 0, list_total = 0, fail_total = 0;
   uint32_t max_primes = 0;
+  uint64_t j_max = 0;
+  const uint64_t ph2 = g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb;
   bool any_per_n = false;
   for (uint32_t r = 0; r < n; ++r) {
     const RangeSpec &s = specs[r];
@@ -205,6 +214,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
     tiles += nt;
     d.n_primes = (s.hi > 1) ? primes_upto(c, host_isqrt(s.hi - 1)) : 0;
     if (nt && d.n_primes > max_primes) max_primes = d.n_primes;
+    if (nt && ph2 && d.jhi) j_max = std::max<uint64_t>(j_max, (2 * d.jhi - 1) / ph2);
     d.per_n_k = s.d_per_n;
     any_per_n |= (s.d_per_n != nullptr);
     d.list_off = list_total;
@@ -227,6 +237,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   ws.max_primes = max_primes;
   ws.list_total = list_total;
   ws.fail_total = fail_total;
+  ws.j_max = j_max;
   ws.any_per_n = any_per_n;
   return SV_OK;
 }
@@ -297,7 +308,7 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     b.bucket_count = ws.bucket_count.p;
     b.bucket_data = ws.bucket_data.p;
     KTimer kt(c, kKBucket, st);
-    SV_TRY_CUDA(launch_bucket_fill(b, ws.max_primes - g.i_large, n, st));
+    SV_TRY_CUDA(launch_bucket_fill(b, ws.max_primes - g.i_large, n, ws.j_max, st));
     kt.done();
     c->launches++;
   }
@@ -390,7 +401,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       b.hdr = ws.hdr.p;
       b.bucket_count = ws.bucket_count.p;
       b.bucket_data = ws.bucket_data.p;
-      e = launch_bucket_fill(b, pt.n - g.i_large, 1u << 20, st);
+      e = launch_bucket_fill(b, pt.n - g.i_large, 1u << 20, 1ull << 23, st);
     }
     if (!e) {
       TileArgs t{};
@@ -729,6 +740,7 @@ void sv_destroy(sv_ctx *c) {
   cudaFree(c->d_mu);
   cudaFree(c->d_inv);
   cudaFree(c->d_lim);
+  cudaFree(c->d_pbits);
   for (auto &k : c->kev) {
     cudaEventDestroy(k.a);
     cudaEventDestroy(k.b);
@@ -750,10 +762,11 @@ sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->d_p && max_hi <= c->max_hi) return SV_OK;
   const uint64_t pmax = host_isqrt(max_hi > 1 ? max_hi - 1 : 1);
-  uint32_t *d_p = nullptr;
+  uint32_t *d_p = nullptr, *d_bits = nullptr;
   uint64_t *d_mu = nullptr, *d_inv = nullptr, *d_lim = nullptr;
+  uint64_t bits_words = 0;
   uint32_t n = 0, n_div = 0;
-  cudaError_t e = build_prime_table(pmax, &d_p, &d_mu, &d_inv, &d_lim, &n, &n_div, c->stream);
+  cudaError_t e = build_prime_table(pmax, &d_p, &d_mu, &d_inv, &d_lim, &d_bits, &bits_words, &n, &n_div, c->stream);
   if (e == cudaErrorMemoryAllocation) return SV_ENOMEM;
   if (e != cudaSuccess) return SV_ECUDA;
   std::vector<uint32_t> hp(n);
@@ -762,6 +775,7 @@ sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
     cudaFree(d_mu);
     cudaFree(d_inv);
     cudaFree(d_lim);
+    cudaFree(d_bits);
     return SV_ECUDA;
   }
   cudaStreamSynchronize(c->stream);
@@ -769,10 +783,13 @@ sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
   cudaFree(c->d_mu);
   cudaFree(c->d_inv);
   cudaFree(c->d_lim);
+  cudaFree(c->d_pbits);
   c->d_p = d_p;
   c->d_mu = d_mu;
   c->d_inv = d_inv;
   c->d_lim = d_lim;
+  c->d_pbits = d_bits;
+  c->pbits_words = bits_words;
   c->n_primes = n;
   c->n_div = n_div;
   c->h_p.swap(hp);

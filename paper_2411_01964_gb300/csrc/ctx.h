@@ -91,6 +91,7 @@ struct Workspace {
   uint32_t strag_cap = 1u << 16;
   uint32_t bucket_cap = 0;
   bool any_per_n = false;
+  uint64_t j_max = 0;  // largest odd-multiplier count of the launch (bucket fill by j)
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
   // the captured launch graph and what it was captured for
   cudaGraphExec_t gexec = nullptr;
@@ -115,6 +116,8 @@ struct sv_ctx {
   uint64_t max_hi = 0, pmax = 0;
   uint32_t *d_p = nullptr;
   uint64_t *d_mu = nullptr, *d_inv = nullptr, *d_lim = nullptr;
+  uint32_t *d_pbits = nullptr;  // odd-prime bitmap of the table's range
+  uint64_t pbits_words = 0;
   uint32_t n_primes = 0, n_div = 0;
   std::vector<uint32_t> h_p;
   std::vector<double> inv_sq_suffix;  // sum over j >= i of 1/p_j^2 (bucket sizing only)

@@ -209,10 +209,13 @@ uint64_t isqrt_host(uint64_t x) {
 // Builds the table of odd primes <= pmax (pmax < 2^32).  Device arrays are
 // allocated here and owned by the caller.
 cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, uint64_t **d_inv,
-                              uint64_t **d_lim, uint32_t *n_out, uint32_t *n_div_out, cudaStream_t st) {
+                              uint64_t **d_lim, uint32_t **d_bits_out, uint64_t *bits_words, uint32_t *n_out,
+                              uint32_t *n_div_out, cudaStream_t st) {
   cudaError_t e;
   *d_p = nullptr;
   *d_mu = *d_inv = *d_lim = nullptr;
+  *d_bits_out = nullptr;
+  *bits_words = 0;
   *n_out = *n_div_out = 0;
   if (pmax < 3) pmax = 3;
   const uint64_t B = isqrt_host(pmax);
@@ -264,6 +267,9 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
   }
   *n_out = h_total;
   *n_div_out = n_div;
+  *d_bits_out = d_bits;  // the bitmap stays: the bucket fill tests primality with it
+  *bits_words = nwords;
+  d_bits = nullptr;
 done:
   cudaFree(d_base);
   cudaFree(d_nbase);

@@ -35,6 +35,8 @@ struct PrimeTab {
   const uint64_t *mu;
   const uint64_t *inv;
   const uint64_t *lim;
+  const uint32_t *bits;  // bit i of the bitmap <-> odd 2i+1 is prime (up to the table's limit)
+  uint64_t bits_words;
   uint32_t n;
   uint32_t n_div;
 };
@@ -99,6 +101,8 @@ struct Geometry {
   uint32_t bucket_cap;
   uint32_t tw_log2;   // log2(tw)
   uint32_t bucket_auto;  // host only: the automatic capacity estimate
+  uint32_t i_hyb;     // primes >= i_hyb reach the buckets by enumerating odd multipliers j
+  uint32_t p_hyb;     // the prime at i_hyb (0xFFFFFFFF: none)
 };
 
 struct TileArgs {
@@ -141,7 +145,9 @@ struct StragArgs {
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t n_tiles, cudaStream_t st);
-cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs,
+// j_max: the largest number of odd multipliers any range of the launch needs
+// for the primes >= p_hyb (sizes the enumeration grid).
+cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs, uint64_t j_max,
                                cudaStream_t st);
 // mode 0: lean scan (lists from k >= 6, no per-n output); 1: general scan;
 // 2: general scan writing the per-n output.
@@ -153,8 +159,8 @@ cudaError_t launch_stragglers(const StragArgs &a, uint32_t grid, cudaStream_t st
 cudaError_t launch_points(PrimeTab pt, const uint64_t *pts, uint64_t count, uint8_t *out,
                           uint32_t grid, cudaStream_t st);
 cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, uint64_t **d_inv,
-                              uint64_t **d_lim, uint32_t *n, uint32_t *n_div,
-                              cudaStream_t st);
+                              uint64_t **d_lim, uint32_t **d_bits, uint64_t *bits_words, uint32_t *n,
+                              uint32_t *n_div, cudaStream_t st);
 
 constexpr int kMaxDensePrimes = 32;  // must match the tile kernel's shared arrays (one warp)
 constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)

@@ -169,15 +169,33 @@ __device__ __forceinline__ void bucket_push(const BucketArgs &a, uint32_t gtile,
     atomicOr(&a.hdr->status, kStBucketOverflow);
 }
 
+// A struck bit J of a range: into the bucket of the tile whose core holds it,
+// and into the next tile's bucket if J also lies in that tile's look-back.
+__device__ __forceinline__ void bucket_emit(const BucketArgs &a, uint64_t J, int64_t w0, uint32_t tile_base,
+                                            uint32_t n_tiles) {
+  const int64_t w = (int64_t)(J >> 5);
+  uint32_t t = 0;
+  if (w >= w0) t = (uint32_t)((uint64_t)(w - w0) >> a.g.tw_log2);
+  if (t >= n_tiles) t = n_tiles - 1;  // cannot happen: J < E
+  const int64_t wst = w0 + (int64_t)t * a.g.tw - (int64_t)a.g.mw;
+  bucket_push(a, tile_base + t, (uint32_t)((int64_t)J - 32 * wst));
+  if (t + 1 < n_tiles) {
+    const int64_t wst1 = wst + (int64_t)a.g.tw;
+    if (w >= wst1) bucket_push(a, tile_base + t + 1, (uint32_t)((int64_t)J - 32 * wst1));
+  }
+}
+
+// Primes i_large <= i < i_hyb: one thread per prime, one Barrett reduction
+// per range for its first struck bit, then every further hit.
 __global__ void __launch_bounds__(256) bucket_fill_kernel(BucketArgs a) {
   __shared__ FillReq s_req[kFillReqChunk];
   const uint32_t n_reqs = a.hdr->n_reqs;
-  const uint32_t max_primes = a.hdr->max_primes;
+  const uint32_t max_primes = min(a.hdr->max_primes, a.g.i_hyb);
   const Geometry g = a.g;
   if (max_primes <= g.i_large) return;
   const uint32_t n_large = max_primes - g.i_large;
   const uint32_t n_pblocks = (n_large + blockDim.x - 1) / blockDim.x;
-  const uint32_t tw = g.tw, mw = g.mw;
+  const uint32_t mw = g.mw;
 
   for (uint32_t pb = blockIdx.x; pb < n_pblocks; pb += gridDim.x) {
     const uint32_t pi = g.i_large + pb * blockDim.x + threadIdx.x;
@@ -208,24 +226,116 @@ __global__ void __launch_bounds__(256) bucket_fill_kernel(BucketArgs a) {
       for (uint32_t r = 0; r < nr; ++r) {
         const FillReq f = s_req[r];
         if (pi >= f.n_primes || f.n_tiles == 0 || f.E <= f.A) continue;
-        for (uint64_t J = f.A + first_strike(f.A, q, mu); J < f.E; J += q) {
-          const int64_t w = (int64_t)(J >> 5);
-          uint32_t t = 0;
-          if (w >= f.w0) t = (uint32_t)((uint64_t)(w - f.w0) >> g.tw_log2);
-          if (t >= f.n_tiles) t = f.n_tiles - 1;  // cannot happen: J < E
-          const int64_t wst = f.w0 + (int64_t)t * tw - (int64_t)mw;
-          bucket_push(a, f.tile_base + t, (uint32_t)((int64_t)J - 32 * wst));
-          if (t + 1 < f.n_tiles) {
-            const int64_t wst1 = wst + (int64_t)tw;
-            if (w >= wst1) bucket_push(a, f.tile_base + t + 1, (uint32_t)((int64_t)J - 32 * wst1));
-          }
+        for (uint64_t J = f.A + first_strike(f.A, q, mu); J < f.E; J += q) bucket_emit(a, J, f.w0, f.tile_base, f.n_tiles);
+      }
+    }
+  }
+}
+
+// floor(sqrt(x)) by Newton's iteration from above (integer only).
+__device__ __forceinline__ uint64_t isqrt_floor(uint64_t x) {
+  if (x < 2) return x;
+  const int bits = 64 - __clzll((long long)x);
+  uint64_t r = 1ull << ((bits + 1) >> 1);  // >= sqrt(x)
+  for (;;) {
+    const uint64_t y = (r + x / r) >> 1;
+    if (y >= r) return r;
+    r = y;
+  }
+}
+
+// Primes p >= p_hyb (index >= i_hyb): instead of reducing the window start
+// modulo every p^2, enumerate the odd multipliers j.  An odd multiple m =
+// j p^2 lies in the window's odd integers [2A+1, 2E-1] exactly when
+// ceil(sqrt(ceil((2A+1)/j))) <= p <= floor(sqrt(floor((2E-1)/j))); the primes
+// of that interval are read from the prime bitmap, 32 candidates per word
+// (four words in flight).  One thread per (range, j); j <= (2E-1) / p_hyb^2.
+__device__ __forceinline__ void emit_word(const BucketArgs &a, const ReqDesc &R, uint32_t m, uint64_t wd, uint64_t j) {
+  while (m) {
+    const uint32_t bb = __ffs(m) - 1;
+    m &= m - 1;
+    const uint64_t p = 2 * (32 * wd + bb) + 1;
+    bucket_emit(a, (p * p * j - 1) >> 1, R.w0, R.tile_base, R.n_tiles);
+  }
+}
+
+constexpr uint64_t kWarpJ = 32;  // odd j < 2 kWarpJ are handled warp-cooperatively
+
+// Bitmap bits [b0, b1] ((p-1)/2) of the odd p >= ph, p <= p_top, with an odd
+// multiple j p^2 in [mlo, mhi]; false if there are none.
+__device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t j, uint64_t ph, uint64_t p_top,
+                                           uint64_t *b0, uint64_t *b1) {
+  const uint64_t lq = (mlo + j - 1) / j, hq = mhi / j;
+  uint64_t plo = isqrt_floor(lq - 1) + 1, phi = isqrt_floor(hq);
+  if (plo < ph) plo = ph;
+  if (phi > p_top) phi = p_top;
+  if (plo > phi) return false;
+  *b0 = plo >> 1;
+  *b1 = (phi - 1) >> 1;
+  return *b0 <= *b1;
+}
+
+__global__ void __launch_bounds__(256) bucket_fill_j_kernel(BucketArgs a) {
+  const uint32_t n_reqs = a.hdr->n_reqs;
+  const Geometry g = a.g;
+  if (a.hdr->max_primes <= g.i_hyb) return;
+  const uint64_t ph = g.p_hyb, ph2 = ph * ph;
+  const uint32_t mw = g.mw;
+  for (uint32_t r = blockIdx.y; r < n_reqs; r += gridDim.y) {
+    const ReqDesc &R = a.reqs[r];
+    if (R.n_tiles == 0 || R.n_primes <= g.i_hyb) continue;
+    const int64_t ws = R.w0 - (int64_t)mw;
+    const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws), E = R.jhi;
+    if (E <= A) continue;
+    const uint64_t mlo = 2 * A + 1, mhi = 2 * E - 1;
+    const uint64_t jmax = mhi / ph2;
+    const uint64_t p_top = a.pt.p[R.n_primes - 1];  // primes with p^2 < hi
+    // the smallest multipliers have the longest p intervals (and the most
+    // hits): one warp per j for j < 2 kWarpJ, lanes striding over the words
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t wpb = blockDim.x >> 5;
+    for (uint64_t t = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < kWarpJ && 2 * t + 1 <= jmax;
+         t += (uint64_t)gridDim.x * wpb) {
+      const uint64_t j = 2 * t + 1;
+      uint64_t b0, b1;
+      if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+      uint64_t w_last = b1 >> 5;
+      if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
+      for (uint64_t w = (b0 >> 5) + lane; w <= w_last; w += 32) {
+        uint32_t mm = a.pt.bits[w];
+        if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
+        if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
+        emit_word(a, R, mm, w, j);
+      }
+    }
+    // the rest: one thread per j
+    for (uint64_t t = kWarpJ + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * t + 1 <= jmax;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t j = 2 * t + 1;
+      uint64_t b0, b1;
+      if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+      const uint64_t w_first = b0 >> 5;
+      uint64_t w_last = b1 >> 5;
+      if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
+      for (uint64_t wd = w_first; wd <= w_last; wd += 4) {
+        uint32_t m[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[u] = (wd + u <= w_last) ? a.pt.bits[wd + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint64_t w = wd + u;
+          if (w > w_last) break;
+          uint32_t mm = m[u];
+          if (w == w_first) mm &= 0xFFFFFFFFu << (b0 & 31);
+          if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
+          emit_word(a, R, mm, w, j);
         }
       }
     }
   }
 }
 
-cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs,
+cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs, uint64_t j_max,
                                cudaStream_t st) {
   if (n_large_max == 0 || n_reqs == 0) return cudaSuccess;
   const uint32_t threads = 256;
@@ -234,6 +344,12 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
   if (gx > 4096) gx = 4096;
   if (gy > 64) gy = 64;
   bucket_fill_kernel<<<dim3(gx, gy), threads, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || a.g.p_hyb == 0xFFFFFFFFu || j_max == 0) return e;
+  uint64_t jx = (j_max / 2 + threads) / threads;  // one thread per odd j
+  if (jx > 64) jx = 64;
+  const uint32_t jy = n_reqs > 1024 ? 1024 : n_reqs;
+  bucket_fill_j_kernel<<<dim3((uint32_t)jx, jy), threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
