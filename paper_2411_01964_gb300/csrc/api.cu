@@ -456,6 +456,33 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
   return SV_OK;
 }
 
+// (n, k) pairs of one range, ascending in n, into out.  The listed n are
+// spread over [lo, hi), so a bucket pass on the position in the range (about
+// one bucket per entry) followed by insertion sorts is linear in practice.
+void sort_by_n(const uint64_t *ns, const uint8_t *ks, uint64_t cnt, uint64_t lo, uint64_t hi,
+               std::vector<std::pair<uint64_t, uint8_t>> &out) {
+  out.resize(cnt);
+  if (cnt < 64 || hi <= lo) {
+    for (uint64_t i = 0; i < cnt; ++i) out[i] = {ns[i], ks[i]};
+    std::sort(out.begin(), out.end());
+    return;
+  }
+  int lb = 0;
+  while ((1ull << lb) < cnt) ++lb;
+  const uint64_t span = hi - lo;
+  const int sb = 64 - __builtin_clzll(span);
+  const int shift = sb > lb ? sb - lb : 0;
+  const uint64_t nb = ((span - 1) >> shift) + 1;
+  std::vector<uint32_t> start(nb + 1, 0);
+  for (uint64_t i = 0; i < cnt; ++i) ++start[((ns[i] - lo) >> shift) + 1];
+  for (uint64_t b = 0; b < nb; ++b) start[b + 1] += start[b];
+  std::vector<uint32_t> fill(start.begin(), start.end() - 1);
+  for (uint64_t i = 0; i < cnt; ++i) out[fill[(ns[i] - lo) >> shift]++] = {ns[i], ks[i]};
+  for (uint64_t b = 0; b < nb; ++b)
+    for (uint32_t i = start[b] + 1; i < start[b + 1]; ++i)
+      for (uint32_t x = i; x > start[b] && out[x - 1].first > out[x].first; --x) std::swap(out[x - 1], out[x]);
+}
+
 enum Collect { kDone, kRetryBucket, kRetryStrag, kRetryList };
 constexpr uint64_t kListRetryMax = 1ull << 26;  // larger lists are returned truncated, unordered
 
@@ -488,6 +515,30 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
       return SV_OK;
     }
   }
+  // one copy of the used parts of the list and failure arenas for all ranges
+  uint64_t list_end = 0, fail_end = 0;
+  for (uint32_t r = 0; r < n; ++r) {
+    if (!outs || !outs[r]) continue;
+    const ReqDesc &d = ws.h_reqs.p[r];
+    const ResultSlot &s = ws.h_slots.p[r];
+    const uint64_t nl = std::min<uint64_t>(s.list_count, d.list_cap);
+    const uint64_t nf = std::min<uint64_t>(s.fail_count, d.fail_cap);
+    if (nl && (outs[r]->list || outs[r]->list_k)) list_end = std::max<uint64_t>(list_end, d.list_off + nl);
+    if (nf && outs[r]->failures) fail_end = std::max<uint64_t>(fail_end, d.fail_off + nf);
+  }
+  if (list_end || fail_end) {
+    if (ws.h_list_n.ensure(list_end ? list_end : 1) || ws.h_list_k.ensure(list_end ? list_end : 1) ||
+        ws.h_fail_n.ensure(fail_end ? fail_end : 1))
+      return SV_ENOMEM;
+    if (list_end) {
+      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_n.p, ws.list_n.p, 8 * list_end, cudaMemcpyDeviceToHost, st));
+      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_k.p, ws.list_k.p, list_end, cudaMemcpyDeviceToHost, st));
+    }
+    if (fail_end) SV_TRY_CUDA(cudaMemcpyAsync(ws.h_fail_n.p, ws.fail_n.p, 8 * fail_end, cudaMemcpyDeviceToHost, st));
+    SV_TRY_CUDA(cudaStreamSynchronize(st));
+    d2h += 9 * list_end + 8 * fail_end;
+  }
+  std::vector<std::pair<uint64_t, uint8_t>> v;
   for (uint32_t r = 0; r < n; ++r) {
     if (!outs || !outs[r]) continue;
     sv_range_result *o = outs[r];
@@ -512,14 +563,7 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
     const ReqDesc &d = ws.h_reqs.p[r];
     const uint64_t nl = std::min<uint64_t>(s.list_count, d.list_cap);
     if (nl && (o->list || o->list_k)) {
-      if (ws.h_list_n.ensure(nl) || ws.h_list_k.ensure(nl)) return SV_ENOMEM;
-      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_n.p, ws.list_n.p + d.list_off, 8 * nl, cudaMemcpyDeviceToHost, st));
-      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_k.p, ws.list_k.p + d.list_off, nl, cudaMemcpyDeviceToHost, st));
-      SV_TRY_CUDA(cudaStreamSynchronize(st));
-      d2h += 9 * nl;
-      std::vector<std::pair<uint64_t, uint8_t>> v(nl);
-      for (uint64_t i = 0; i < nl; ++i) v[i] = {ws.h_list_n.p[i], ws.h_list_k.p[i]};
-      std::sort(v.begin(), v.end());
+      sort_by_n(ws.h_list_n.p + d.list_off, ws.h_list_k.p + d.list_off, nl, sp.lo, sp.hi, v);
       const uint64_t m = std::min<uint64_t>(nl, o->list_cap);
       for (uint64_t i = 0; i < m; ++i) {
         if (o->list) o->list[i] = v[i].first;
@@ -528,13 +572,10 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
     }
     const uint64_t nf = std::min<uint64_t>(s.fail_count, d.fail_cap);
     if (nf && o->failures) {
-      if (ws.h_fail_n.ensure(nf)) return SV_ENOMEM;
-      SV_TRY_CUDA(cudaMemcpyAsync(ws.h_fail_n.p, ws.fail_n.p + d.fail_off, 8 * nf, cudaMemcpyDeviceToHost, st));
-      SV_TRY_CUDA(cudaStreamSynchronize(st));
-      d2h += 8 * nf;
-      std::sort(ws.h_fail_n.p, ws.h_fail_n.p + nf);
+      uint64_t *f = ws.h_fail_n.p + d.fail_off;
+      std::sort(f, f + nf);
       const uint64_t m = std::min<uint64_t>(nf, o->fail_cap);
-      std::memcpy(o->failures, ws.h_fail_n.p, 8 * m);
+      std::memcpy(o->failures, f, 8 * m);
     }
   }
   ws.d2h_bytes = d2h;
