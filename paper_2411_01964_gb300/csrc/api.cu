@@ -126,8 +126,8 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   g.kwin = k.margin_log2;
   g.rec_t = k.record_k_threshold;
   g.i_med = k.stamp_primes;  // the stamped primes are the table's first entries
-  // dense: at least 32 strikes in a full window of 32*(tw+mw) bits
-  const uint64_t dense_q = (uint64_t)g.tw + g.mw;
+  // dense: at least kDenseMinHits strikes in a full window of 32*(tw+mw) bits
+  const uint64_t dense_q = 32ull * ((uint64_t)g.tw + g.mw) / (uint64_t)kDenseMinHits;
   uint32_t i = g.i_med;
   while (i < c->n_primes && i < g.i_med + (uint32_t)kMaxDensePrimes && (uint64_t)c->h_p[i] * c->h_p[i] <= dense_q)
     ++i;

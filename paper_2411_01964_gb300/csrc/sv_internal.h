@@ -162,7 +162,8 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
                               uint64_t **d_lim, uint32_t **d_bits, uint64_t *bits_words, uint32_t *n,
                               uint32_t *n_div, cudaStream_t st);
 
-constexpr int kMaxDensePrimes = 32;  // must match the tile kernel's shared arrays (one warp)
+constexpr int kMaxDensePrimes = 128;  // must match the tile kernel's shared arrays (four warps)
+constexpr int kDenseMinHits = 2;      // primes with at least this many strikes per window are "dense"
 constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)
 
 }  // namespace sv

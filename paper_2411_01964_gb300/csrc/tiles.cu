@@ -9,9 +9,10 @@
 //              patterns of the NS smallest odd primes (computed by the word's
 //              owner, not loaded; NS = sv_config.stamp_primes);
 //   2. strike: the next primes up to large_prime_min clear their odd multiples of
-//              p^2 with shared-memory atomicAnd: "dense" primes (>= 32 hits
-//              per window) have their strikes spread over all threads of the
-//              CTA, sparser ones take one thread per prime; larger primes
+//              p^2 with shared-memory atomicAnd: "dense" primes (>= 2 hits
+//              per window, at most 128 primes) have their strikes numbered and
+//              split evenly over all threads of the CTA, sparser ones take
+//              one thread per prime; larger primes
 //              arrive as precomputed bit offsets in the tile's bucket
 //              (bucket_fill_kernel);
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
@@ -69,31 +70,76 @@ __device__ __forceinline__ uint32_t stamp_step(uint32_t j, uint32_t d, uint32_t 
   return (j >= d) ? (j - d) : (j + q - d);
 }
 
-// Window words [nz, nwords) <- AND of the NS stamped patterns; thread tid
-// takes words tid, tid + S, ...  j[s] is the offset of prime s's first struck
-// bit in the current word (>= 32: none); moving S words subtracts 32*S mod q.
+// The first stamped primes come from two periodic tables in shared memory.
+// The strike pattern of a set of primes on the 32 bits of word a depends only
+// on a mod P, P the product of their squares (odd, so 32 is invertible mod P):
+// entry e of a table is the pattern of the words a = e (mod P).  Table A
+// holds {3, 11} (P = 1089) and table B {5, 7} (P = 1225), or A alone {3, 5}
+// (P = 225) when only two primes are stamped.  Consecutive words read
+// consecutive entries, so a warp's reads hit distinct banks.
 template <int NS>
-__device__ __forceinline__ void stamp_window(uint32_t *win, uint32_t nz, uint32_t nwords, int64_t wstart) {
+struct StampTab {
+  static constexpr bool kTwo = NS >= 4;                   // two tables
+  static constexpr uint32_t kQa0 = 9, kQa1 = kTwo ? 121u : 25u;
+  static constexpr uint32_t kQb0 = 25, kQb1 = 49;
+  static constexpr uint32_t kPa = kQa0 * kQa1;
+  static constexpr uint32_t kPb = kTwo ? kQb0 * kQb1 : 0u;
+  static constexpr uint32_t kSize = kPa + kPb;
+  static constexpr int kCovered = kTwo ? 4 : 2;           // stamp_p(0 .. kCovered-1)
+};
+
+// The pattern of the odd multiples of q on the word starting at bit J.
+__device__ __forceinline__ uint32_t stamp_pattern(uint32_t J, uint32_t q) {
+  uint32_t rep = 0;
+  for (uint32_t b = 0; b < 32; b += q) rep |= 1u << b;
+  return __funnelshift_lc(0u, rep, stamp_first(J, q));
+}
+
+template <int NS>
+__device__ __forceinline__ void build_stamp_tables(uint32_t *tab) {
+  using T = StampTab<NS>;
+  for (uint32_t e = threadIdx.x; e < T::kSize; e += blockDim.x) {
+    uint32_t v;
+    if (e < T::kPa) v = stamp_pattern(32u * e, T::kQa0) | stamp_pattern(32u * e, T::kQa1);
+    else v = stamp_pattern(32u * (e - T::kPa), T::kQb0) | stamp_pattern(32u * (e - T::kPa), T::kQb1);
+    tab[e] = v;
+  }
+}
+
+// Window words [nz, nwords) <- AND of the NS stamped patterns; thread tid
+// takes words tid, tid + S, ...  The table positions advance by S mod P; the
+// primes beyond the tables keep j[s], the offset of their first struck bit in
+// the current word (>= 32: none), which moving S words lowers by 32*S mod q.
+template <int NS>
+__device__ __forceinline__ void stamp_window(uint32_t *win, const uint32_t *tab, uint32_t nz, uint32_t nwords,
+                                             int64_t wstart) {
+  using T = StampTab<NS>;
+  constexpr int NX = NS - T::kCovered;
   const uint32_t S = blockDim.x;
   uint32_t i = nz + threadIdx.x;
   if (i >= nwords) return;
-  const uint64_t abit = 32ull * (uint64_t)(wstart + (int64_t)i);
-  uint32_t j[NS], d[NS];
+  const uint64_t aw = (uint64_t)(wstart + (int64_t)i);  // >= 0 since i >= nz
+  uint32_t ea = (uint32_t)(aw % T::kPa), eb = T::kTwo ? (uint32_t)(aw % (T::kTwo ? T::kPb : 1u)) : 0u;
+  const uint32_t sa = S % T::kPa, sb = T::kTwo ? S % (T::kTwo ? T::kPb : 1u) : 0u;
+  uint32_t j[NX > 0 ? NX : 1], d[NX > 0 ? NX : 1];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const uint32_t q = stamp_p(s) * stamp_p(s);
-    j[s] = stamp_first(abit, q);
+  for (int s = 0; s < NX; ++s) {
+    const uint32_t q = stamp_p(T::kCovered + s) * stamp_p(T::kCovered + s);
+    j[s] = stamp_first(32ull * aw, q);
     d[s] = (32u * S) % q;
   }
   for (; i < nwords; i += S) {
-    uint32_t m = 0;
+    uint32_t m = tab[ea];
+    if (T::kTwo) m |= tab[T::kPa + eb];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const uint32_t q = stamp_p(s) * stamp_p(s);
+    for (int s = 0; s < NX; ++s) {
+      const uint32_t q = stamp_p(T::kCovered + s) * stamp_p(T::kCovered + s);
       m |= __funnelshift_lc(0u, stamp_rep(q), j[s]);
       j[s] = stamp_step(j[s], d[s], q);
     }
     win[i] = ~m;
+    ea = min(ea + sa, ea + sa - T::kPa);  // unsigned: subtracts P once the sum reaches it
+    if (T::kTwo) eb = min(eb + sb, eb + sb - T::kPb);
   }
 }
 
@@ -355,7 +401,7 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
 
 // The tile kernel.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kMaxDense = 32;  // dense primes (>= 32 strikes per window) per tile: one warp
+constexpr uint32_t kMaxDense = kMaxDensePrimes;  // dense primes per tile: four warps, one prime per lane
 
 constexpr uint32_t kDeferCap = 128;  // words left unresolved after k = 5, per tile
 constexpr uint32_t kMaxSparse = kMaxSparsePrimes;  // primes struck one thread each, per tile
@@ -371,11 +417,14 @@ struct ScanShared {
   uint32_t need;                   // k <= 5 whose first occurrence this tile may still improve
   uint32_t defer_n;
   // the dense primes' strikes of this tile, numbered consecutively prime by
-  // prime: prime d owns numbers [dense_pre[d], dense_pre[d+1]), its strike
-  // number x is bit dense_off[d] + (x - dense_pre[d]) * dense_q[d]
+  // prime: prime d owns numbers [pre(d), pre(d+1)), its strike number x is
+  // bit dense_off[d] + (x - pre(d)) * dense_q[d].  pre(d) = dense_pre[d] (the
+  // exclusive prefix within d's group of 32) + the strikes of groups < d/32
+  // (dense_grp[g] = strikes of group g).
   uint32_t dense_q[kMaxDense];
   uint32_t dense_off[kMaxDense];
-  uint32_t dense_pre[kMaxDense + 1];
+  uint32_t dense_pre[kMaxDense];
+  uint32_t dense_grp[kMaxDense / 32];
   uint32_t defer_i[kDeferCap];     // window index of a deferred word
   uint32_t defer_u[kDeferCap];     // its n still unresolved after k = 5
   uint32_t sparse_off[kMaxSparse]; // first struck bit of each sparse prime (>= nbits: none)
@@ -668,6 +717,7 @@ template <int MODE, int NS>
 __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
   extern __shared__ uint32_t win[];
   __shared__ ScanShared sh;
+  __shared__ uint32_t stab[StampTab<NS>::kSize];
   constexpr bool LEAN = (MODE == 0);
   constexpr bool PER_N = (MODE == 2);
 
@@ -684,6 +734,7 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     sh.hist[tid] = 0ull;
     sh.first[tid] = kNoN;
   }
+  build_stamp_tables<NS>(stab);
   if (tid == 0) {
     sh.n_strag = 0;
     sh.defer_n = 0;
@@ -738,26 +789,27 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       for (uint32_t k = 1; k <= kfirst; ++k) known[k - 1] = __ldcg(&a.slots[R.slot].first_n[k]);
 
     // ---- 1. stamp the smallest primes; the dense primes' first strikes -------
-    if (warp == 0) {
+    if (warp < kMaxDense / 32) {  // blockDim.x >= 128: warps 0..3 exist
+      const uint32_t d = 32u * warp + lane;
       uint32_t q = 1, off = 0, cnt = 0;
-      if (lane < nd) {
-        const uint64_t p = a.pt.p[g.i_med + lane];
+      if (d < nd) {
+        const uint64_t p = a.pt.p[g.i_med + d];
         q = (uint32_t)(p * p);
-        off = abias + (uint32_t)first_strike(A, (uint64_t)q, a.pt.mu[g.i_med + lane]);
+        off = abias + (uint32_t)first_strike(A, (uint64_t)q, a.pt.mu[g.i_med + d]);
         cnt = off < nbits ? (nbits - off + q - 1) / q : 0u;
       }
-      uint32_t incl = cnt;  // inclusive prefix over the dense primes
+      uint32_t incl = cnt;  // inclusive prefix within the group of 32
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= (uint32_t)o) incl += y;
       }
-      if (lane < nd) {
-        sh.dense_q[lane] = q;
-        sh.dense_off[lane] = off;
-        sh.dense_pre[lane] = incl - cnt;
+      if (d < nd) {
+        sh.dense_q[d] = q;
+        sh.dense_off[d] = off;
+        sh.dense_pre[d] = incl - cnt;
       }
-      if (lane == 31) sh.dense_pre[nd] = incl;  // lanes >= nd add nothing: the total
+      if (lane == 31) sh.dense_grp[warp] = incl;  // lanes with d >= nd add nothing
     }
     const uint32_t nz = (wstart < 0) ? (uint32_t)min((int64_t)nwords, -wstart) : 0u;
     for (uint32_t i = tid; i < nz; i += S) win[i] = 0u;  // integers below 1
@@ -775,7 +827,7 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     const uint32_t nb = min(a.bucket_count[gt], g.bucket_cap);
     const uint32_t bv0 = tid < g.bucket_cap ? bd[tid] : 0u;
     const uint32_t bv1 = tid + S < g.bucket_cap ? bd[tid + S] : 0u;
-    stamp_window<NS>(win, nz, nwords, wstart);
+    stamp_window<NS>(win, stab, nz, nwords, wstart);
     if (tid == 0) {
       uint32_t need = 0;
       for (uint32_t k = 1; k <= kfirst; ++k)
@@ -787,23 +839,29 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     // ---- 2. strikes: dense primes spread over all threads, sparse primes one
     //         thread each, large primes from the tile's bucket ---------------
     {
-      // dense primes: warp w takes strike numbers [X w / nwarps, X (w+1) / nwarps),
-      // its lanes every 32nd; the prime d of a number only moves forward
-      const uint32_t nwarps = S >> 5;
-      const uint32_t X = sh.dense_pre[nd];
-      const uint32_t x1 = (X * (warp + 1)) / nwarps;
-      uint32_t x = (X * warp) / nwarps + lane;
+      // dense primes: thread tid takes the strike numbers [X tid / S, X (tid+1) / S);
+      // the prime d of a number only moves forward
+      const uint32_t g1 = sh.dense_grp[0], g2 = g1 + sh.dense_grp[1], g3 = g2 + sh.dense_grp[2];
+      const uint32_t X = g3 + sh.dense_grp[3];
+      auto pre = [&](uint32_t d) -> uint32_t {
+        if (d >= nd) return X;
+        const uint32_t gs = d >> 5;
+        return sh.dense_pre[d] + (gs == 0 ? 0u : gs == 1 ? g1 : gs == 2 ? g2 : g3);
+      };
+      uint32_t x = (uint32_t)(((uint64_t)X * tid) / S);
+      const uint32_t x1 = (uint32_t)(((uint64_t)X * (tid + 1)) / S);
       if (x < x1) {
-        uint32_t d = 0;
-        while (sh.dense_pre[d + 1] <= x) ++d;
-        uint32_t pn = sh.dense_pre[d + 1], p0 = sh.dense_pre[d], q = sh.dense_q[d], off = sh.dense_off[d];
-        for (; x < x1; x += 32u) {
-          if (x >= pn) {
-            do {
-              ++d;
-              pn = sh.dense_pre[d + 1];
-            } while (x >= pn);
-            p0 = sh.dense_pre[d];
+        uint32_t lo = 0, hi = nd;  // the largest d with pre(d) <= x: pre(lo) <= x < pre(hi)
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (pre(mid) <= x) lo = mid; else hi = mid;
+        }
+        uint32_t d = lo, p0 = pre(d), pn = pre(d + 1), q = sh.dense_q[d], off = sh.dense_off[d];
+        for (; x < x1; ++x) {
+          while (x >= pn) {
+            ++d;
+            p0 = pn;
+            pn = pre(d + 1);
             q = sh.dense_q[d];
             off = sh.dense_off[d];
           }
@@ -894,31 +952,40 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
 // The stamped-prime counts instantiated (sv_config.stamp_primes).
 #define SV_FOR_EACH_NS(X) X(2) X(4) X(6) X(8)
 
-static int g_max_dyn_smem = 0;
+static bool g_tile_smem_set = false;
+
+// Raise one instantiation's dynamic shared memory limit to what its static
+// shared memory leaves of the opt-in limit.
+template <class K>
+static cudaError_t set_max_dyn(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
 
 cudaError_t tile_kernel_setup(size_t smem) {
   // The attribute is per kernel and process wide: raise it once to the
-  // largest window any configuration may use (the opt-in limit minus the
-  // static shared memory), so contexts with different tiles never disagree.
+  // largest window any configuration may use, so contexts with different
+  // tiles never disagree.
   (void)smem;
-  if (g_max_dyn_smem) return cudaSuccess;
+  if (g_tile_smem_set) return cudaSuccess;
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-  const int max_dyn = optin - (int)sizeof(ScanShared) - 1024;
-#define SV_SET(NS)                                                                                    \
-  if ((e = cudaFuncSetAttribute(tile_kernel<0, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) || \
-      (e = cudaFuncSetAttribute(tile_kernel<1, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)) || \
-      (e = cudaFuncSetAttribute(tile_kernel<2, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn)))   \
+#define SV_SET(NS)                                                                 \
+  if ((e = set_max_dyn(tile_kernel<0, NS>, optin)) || (e = set_max_dyn(tile_kernel<1, NS>, optin)) || \
+      (e = set_max_dyn(tile_kernel<2, NS>, optin)))                               \
     return e;
   SV_FOR_EACH_NS(SV_SET)
 #undef SV_SET
-  g_max_dyn_smem = max_dyn;
+  g_tile_smem_set = true;
   return cudaSuccess;
 }
 
-size_t tile_static_smem() { return sizeof(ScanShared); }
+// An upper bound of the tile kernel's static shared memory (all instantiations).
+size_t tile_static_smem() { return sizeof(ScanShared) + 4 * StampTab<8>::kSize + 256; }
 
 cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem, int mode, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
