@@ -412,6 +412,8 @@ struct ScanShared {
   ReqDesc req;
   uint32_t tile;
   uint32_t next_tile;              // prefetched during the previous tile's scan
+  uint32_t chunk_end;              // end of the chunk of consecutive tiles being worked
+  uint32_t fresh;                  // 1: the primes' offsets are computed, not carried
   uint32_t req_idx;
   uint32_t n_strag;                // stragglers this tile sent to the exact test
   uint32_t need;                   // k <= 5 whose first occurrence this tile may still improve
@@ -425,6 +427,7 @@ struct ScanShared {
   uint32_t dense_off[kMaxDense];
   uint32_t dense_pre[kMaxDense];
   uint32_t dense_grp[kMaxDense / 32];
+  uint32_t dense_tq[kMaxDense];    // (32 tw) mod dense_q: a window's shift, reduced
   uint32_t defer_i[kDeferCap];     // window index of a deferred word
   uint32_t defer_u[kDeferCap];     // its n still unresolved after k = 5
   uint32_t sparse_off[kMaxSparse]; // first struck bit of each sparse prime (>= nbits: none)
@@ -631,6 +634,24 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
   const uint32_t mw = a.g.mw;
   uint32_t need = sh.need;
   uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  if (need == 0u && ifl <= mw && nfull >= nwords - ifl && ((nwords - mw) & 63u) == 0u) {
+    // every core word is in range and fully valid, and no first occurrence
+    // is searched: no masks, no bounds checks
+    for (uint32_t ib = mw + warp * 64u; ib < nwords; ib += nwarps * 64u) {
+      const uint32_t i0 = ib + lane, i1 = i0 + 32u;
+      const uint32_t w0 = win[i0], p0 = win[i0 - 1], w1 = win[i1], p1 = win[i1 - 1];
+      uint32_t u0 = ~__funnelshift_l(p0, w0, 1);
+      uint32_t u1 = ~__funnelshift_l(p1, w1, 1);
+      c2 += step2<2>(p0, w0, p1, w1, u0, u1);
+      c3 += step2<3>(p0, w0, p1, w1, u0, u1);
+      c4 += step2<4>(p0, w0, p1, w1, u0, u1);
+      if (__any_sync(0xFFFFFFFFu, u0 | u1)) {
+        c5 += step2<5>(p0, w0, p1, w1, u0, u1);
+        if (u0) defer_word(win, i0, u0, wstart + (int64_t)i0, a, sh);
+        if (u1) defer_word(win, i1, u1, wstart + (int64_t)i1, a, sh);
+      }
+    }
+  } else
   for (uint32_t ib = mw + warp * 64u; ib < nwords; ib += nwarps * 64u) {
     const uint32_t i0 = ib + lane, i1 = i0 + 32u;
     const bool a0 = i0 < nwords, a1 = i1 < nwords;
@@ -711,6 +732,27 @@ __device__ __forceinline__ void scan_tile(const uint32_t *win, const TileArgs &a
   }
 }
 
+// The tile queue hands out chunks of consecutive tiles, so that one CTA works
+// a range's tiles in order and the primes' offsets carry from one window to
+// the next; the last 4 tiles per CTA go one at a time, which keeps the CTAs'
+// finishing times within about one tile of each other.  Chunk j is tiles
+// [*s, *e).
+constexpr uint32_t kChunk = 8;
+__device__ __forceinline__ void chunk_range(uint32_t j, uint32_t total, uint32_t ctas, uint32_t *s, uint32_t *e) {
+  const uint32_t reserve = 4u * ctas;
+  const uint32_t n_big = total > reserve ? (total - reserve) / kChunk : 0u;
+  uint64_t b, f;
+  if (j < n_big) {
+    b = (uint64_t)j * kChunk;
+    f = b + kChunk;
+  } else {
+    b = (uint64_t)n_big * kChunk + (j - n_big);
+    f = b + 1;
+  }
+  *s = (uint32_t)min(b, (uint64_t)total);
+  *e = (uint32_t)min(f, (uint64_t)total);
+}
+
 // MODE 0: lean scan (no per-n output, lists from k >= 6); 1: general scan;
 // 2: general scan with the per-n output.  NS: number of stamped primes.
 template <int MODE, int NS>
@@ -735,39 +777,60 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     sh.first[tid] = kNoN;
   }
   build_stamp_tables<NS>(stab);
+  const uint32_t T = 32u * g.tw;  // a window starts T bits above the previous one
   if (tid == 0) {
     sh.n_strag = 0;
     sh.defer_n = 0;
     sh.req_idx = 0xFFFFFFFFu;
-    sh.next_tile = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+    uint32_t cs, ce;
+    chunk_range((uint32_t)atomicAdd(&a.hdr->work_counter, 1ull), total, gridDim.x, &cs, &ce);
+    sh.next_tile = cs;
+    sh.chunk_end = ce;
+    sh.tile = 0xFFFFFFFFu;
   }
   __syncthreads();
 
   for (;;) {
     if (tid == 0) {
       const uint32_t t = sh.next_tile;
+      uint32_t fresh = sh.tile == 0xFFFFFFFFu || t != sh.tile + 1u;  // not the previous tile's successor
       sh.tile = t;
-      if (t < total) {
-        uint32_t lo = 0, hi = n_reqs;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (a.reqs[mid].tile_base <= t) lo = mid; else hi = mid;
+      const uint32_t r = sh.req_idx;
+      if (t < total && (r == 0xFFFFFFFFu || t - sh.req.tile_base >= sh.req.n_tiles)) {
+        // the range of tile t: the next one, else a search
+        uint32_t lo;
+        if (r != 0xFFFFFFFFu && r + 1u < n_reqs && a.reqs[r + 1u].tile_base <= t &&
+            t - a.reqs[r + 1u].tile_base < a.reqs[r + 1u].n_tiles) {
+          lo = r + 1u;
+        } else {
+          uint32_t hi = n_reqs;
+          lo = 0;
+          while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.reqs[mid].tile_base <= t) lo = mid; else hi = mid;
+          }
         }
-        if (lo != sh.req_idx) {
-          sh.req_idx = lo;
-          sh.req = a.reqs[lo];
-        }
+        sh.req_idx = lo;
+        sh.req = a.reqs[lo];
+        fresh = 1;
       }
+      sh.fresh = fresh;
     }
     __syncthreads();
     const uint32_t gt = sh.tile;
     if (gt >= total) break;
     const ReqDesc &R = sh.req;
     const uint32_t t = gt - R.tile_base;
+    const bool fresh = sh.fresh != 0;
     if (t >= R.n_tiles) {  // bounds check: never expected
       if (tid == 0) {
         atomicOr(&a.hdr->status, kStBadTile);
-        sh.next_tile = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+        sh.req_idx = 0xFFFFFFFFu;
+        sh.tile = 0xFFFFFFFFu;
+        uint32_t cs, ce;
+        chunk_range((uint32_t)atomicAdd(&a.hdr->work_counter, 1ull), total, gridDim.x, &cs, &ce);
+        sh.next_tile = cs;
+        sh.chunk_end = ce;
       }
       __syncthreads();
       continue;
@@ -793,9 +856,18 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       const uint32_t d = 32u * warp + lane;
       uint32_t q = 1, off = 0, cnt = 0;
       if (d < nd) {
-        const uint64_t p = a.pt.p[g.i_med + d];
-        q = (uint32_t)(p * p);
-        off = abias + (uint32_t)first_strike(A, (uint64_t)q, a.pt.mu[g.i_med + d]);
+        if (fresh) {
+          const uint64_t p = a.pt.p[g.i_med + d];
+          q = (uint32_t)(p * p);
+          off = abias + (uint32_t)first_strike(A, (uint64_t)q, a.pt.mu[g.i_med + d]);
+          sh.dense_tq[d] = T % q;
+        } else {
+          // the previous window began T bits lower: off = (off_prev - T) mod q
+          q = sh.dense_q[d];
+          off = sh.dense_off[d] + q - sh.dense_tq[d];
+          if (off >= q) off -= q;
+          if (off >= q) off %= q;  // only after a window that began below bit 0
+        }
         cnt = off < nbits ? (nbits - off + q - 1) / q : 0u;
       }
       uint32_t incl = cnt;  // inclusive prefix within the group of 32
@@ -813,11 +885,12 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     }
     const uint32_t nz = (wstart < 0) ? (uint32_t)min((int64_t)nwords, -wstart) : 0u;
     for (uint32_t i = tid; i < nz; i += S) win[i] = 0u;  // integers below 1
-    // sparse primes: their first strikes, and the tile's bucket entries, are
-    // fetched here so that the global-memory latency overlaps the stamping
+    // sparse primes: their first strikes (on a fresh tile; otherwise carried
+    // from the previous window), and the tile's bucket entries, are fetched
+    // here so that the global-memory latency overlaps the stamping
     const uint32_t i_large = min(g.i_large, max(R.n_primes, g.i_dense));
     const uint32_t n_sparse = i_large - g.i_dense;  // <= kMaxSparse (host guarantees)
-    for (uint32_t j = tid; j < n_sparse; j += S) {
+    if (fresh) for (uint32_t j = tid; j < n_sparse; j += S) {
       const uint64_t p = a.pt.p[g.i_dense + j];
       const uint64_t q = p * p;
       sh.sparse_off[j] = abias + (uint32_t)first_strike(A, q, a.pt.mu[g.i_dense + j]);
@@ -848,8 +921,8 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
         const uint32_t gs = d >> 5;
         return sh.dense_pre[d] + (gs == 0 ? 0u : gs == 1 ? g1 : gs == 2 ? g2 : g3);
       };
-      uint32_t x = (uint32_t)(((uint64_t)X * tid) / S);
-      const uint32_t x1 = (uint32_t)(((uint64_t)X * (tid + 1)) / S);
+      uint32_t x = (X * tid) / S;  // X * S < 2^32: at most ~2^15 strikes per window
+      const uint32_t x1 = (X * (tid + 1u)) / S;
       if (x < x1) {
         uint32_t lo = 0, hi = nd;  // the largest d with pre(d) <= x: pre(lo) <= x < pre(hi)
         while (hi - lo > 1) {
@@ -868,9 +941,19 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
           strike(win, off + (x - p0) * q);
         }
       }
+      // a full window's strikes carry to the next window: its first struck
+      // bit is the first one >= T, shifted down by T (q exceeds the margin,
+      // so at most a few subtractions remain)
+      const bool carry = nwords == g.tw + g.mw;
       for (uint32_t j = tid; j < n_sparse; j += S) {
         const uint32_t q = sh.sparse_q[j];
-        for (uint32_t b = sh.sparse_off[j]; b < nbits; b += q) strike(win, b);
+        uint32_t b = sh.sparse_off[j];
+        for (; b < nbits; b += q) strike(win, b);
+        if (carry) {
+          b -= T;
+          while (b >= q) b -= q;
+          sh.sparse_off[j] = b;
+        }
       }
       for (uint32_t e = tid; e < nb; e += S) {
         const uint32_t b = e < S ? bv0 : (e < 2 * S ? bv1 : bd[e]);
@@ -880,9 +963,17 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     }
     __syncthreads();
 
-    // the next tile's index, fetched while this tile is scanned
-    uint32_t next = 0;
-    if (tid == 0) next = (uint32_t)atomicAdd(&a.hdr->work_counter, 1ull);
+    // the next tile's index (the chunk's next tile, else a new chunk's first),
+    // fetched while this tile is scanned
+    uint32_t next = 0, next_end = 0;
+    if (tid == 0) {
+      if (gt + 1u < sh.chunk_end) {
+        next = gt + 1u;
+        next_end = sh.chunk_end;
+      } else {
+        chunk_range((uint32_t)atomicAdd(&a.hdr->work_counter, 1ull), total, gridDim.x, &next, &next_end);
+      }
+    }
 
     if (R.sieve_only) {
       // ---- Algorithm 1 alone: write the core words ------------------------
@@ -904,7 +995,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       else
         scan_tile<LEAN, PER_N>(win, a, sh, wstart, nwords, ifl, nfull);
     }
-    if (tid == 0) sh.next_tile = next;
+    if (tid == 0) {
+      sh.next_tile = next;
+      sh.chunk_end = next_end;
+    }
     __syncthreads();
     if (LEAN) {
       // words that were still unresolved after k = 5
