@@ -403,7 +403,7 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
 // ---------------------------------------------------------------------------
 constexpr uint32_t kMaxDense = kMaxDensePrimes;  // dense primes per tile: four warps, one prime per lane
 
-constexpr uint32_t kDeferCap = 128;  // words left unresolved after k = 5, per tile
+constexpr uint32_t kLstCap = 128;  // list entries (mink >= T) buffered per tile
 constexpr uint32_t kMaxSparse = kMaxSparsePrimes;  // primes struck one thread each, per tile
 
 struct ScanShared {
@@ -417,7 +417,7 @@ struct ScanShared {
   uint32_t req_idx;
   uint32_t n_strag;                // stragglers this tile sent to the exact test
   uint32_t need;                   // k <= 5 whose first occurrence this tile may still improve
-  uint32_t defer_n;
+  uint32_t lst_cnt;                // list entries this tile found (buffered up to kLstCap)
   // the dense primes' strikes of this tile, numbered consecutively prime by
   // prime: prime d owns numbers [pre(d), pre(d+1)), its strike number x is
   // bit dense_off[d] + (x - pre(d)) * dense_q[d].  pre(d) = dense_pre[d] (the
@@ -428,8 +428,8 @@ struct ScanShared {
   uint32_t dense_pre[kMaxDense];
   uint32_t dense_grp[kMaxDense / 32];
   uint32_t dense_tq[kMaxDense];    // (32 tw) mod dense_q: a window's shift, reduced
-  uint32_t defer_i[kDeferCap];     // window index of a deferred word
-  uint32_t defer_u[kDeferCap];     // its n still unresolved after k = 5
+  unsigned long long lst_n[kLstCap];  // the buffered list entries: n and mink
+  uint8_t lst_k[kLstCap];
   uint32_t sparse_off[kMaxSparse]; // first struck bit of each sparse prime (>= nbits: none)
   uint32_t sparse_q[kMaxSparse];
 };
@@ -582,8 +582,27 @@ __device__ __forceinline__ void scan_word(const uint32_t *win, uint32_t i, bool 
   if (PER_N && sh.req.per_n_k) write_per_n(sh.req.per_n_k, 32ull * (uint64_t)aw, sh.req.jlo, valid, pl);
 }
 
+// List entries (n with mink = k >= T) go to the tile's shared buffer; the
+// tile's flush reserves their place in the range's list with one atomic,
+// and they are copied out during the next tile's stamping.  Entries beyond
+// the buffer go straight to the list.
+__device__ __noinline__ void list_buffer(const TileArgs &a, ScanShared &sh, uint32_t hit, uint64_t J0, uint32_t k) {
+  while (hit) {
+    const uint32_t b = __ffs(hit) - 1;
+    const uint32_t e = atomicAdd(&sh.lst_cnt, 1u);
+    if (e < kLstCap) {
+      sh.lst_n[e] = 2ull * (J0 + b) + 1ull;
+      sh.lst_k[e] = (uint8_t)k;
+    } else {
+      list_append(a, sh.req, 1u << b, J0, k);
+    }
+    hit &= hit - 1;
+  }
+}
+
 // One thread finishes one word whose n (bits u) are unresolved after k = 5:
 // k = 6 .. kwin by whole-word look-back, then the exact test for the rest.
+// First occurrences of every k go to the tile's shared minima.
 __device__ __noinline__ void finish_word(const uint32_t *win, uint32_t i, uint32_t u, int64_t aw, const TileArgs &a,
                                          ScanShared &sh) {
   const uint64_t J0 = 32ull * (uint64_t)aw;
@@ -593,24 +612,11 @@ __device__ __noinline__ void finish_word(const uint32_t *win, uint32_t i, uint32
     u ^= h;
     if (h) {
       atomicAdd(&sh.hist[k], (unsigned long long)__popc(h));
-      if (k < rec_t)
-        atomicMin(&sh.first[k], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(h) - 1)) + 1ull));
-      else
-        list_append(a, sh.req, h, J0, k);
+      atomicMin(&sh.first[k], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(h) - 1)) + 1ull));
+      if (k >= rec_t) list_buffer(a, sh, h, J0, k);
     }
   }
   if (u) straggler_push(a, sh, u, J0, kwin + 1u);
-}
-
-__device__ __forceinline__ void defer_word(const uint32_t *win, uint32_t i, uint32_t u, int64_t aw, const TileArgs &a,
-                                           ScanShared &sh) {
-  const uint32_t e = atomicAdd(&sh.defer_n, 1u);
-  if (e < kDeferCap) {
-    sh.defer_i[e] = i;
-    sh.defer_u[e] = u;
-  } else {
-    finish_word(win, i, u, aw, a, sh);
-  }
 }
 
 // k = K for two words at once (independent chains for the scheduler).
@@ -634,6 +640,15 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
   const uint32_t mw = a.g.mw;
   uint32_t need = sh.need;
   uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  // a word still unresolved after k = 5 waits in its lane (one at most; an
+  // earlier one is finished first) and is finished after the loop
+  uint32_t pend_i = 0, pend_u = 0;
+#define SV_DEFER(I, U)                                                              \
+  if (U) {                                                                          \
+    if (pend_u) finish_word(win, pend_i, pend_u, wstart + (int64_t)pend_i, a, sh); \
+    pend_i = (I);                                                                   \
+    pend_u = (U);                                                                   \
+  }
   if (need == 0u && ifl <= mw && nfull >= nwords - ifl && ((nwords - mw) & 63u) == 0u) {
     // every core word is in range and fully valid, and no first occurrence
     // is searched: no masks, no bounds checks
@@ -647,8 +662,8 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
       c4 += step2<4>(p0, w0, p1, w1, u0, u1);
       if (__any_sync(0xFFFFFFFFu, u0 | u1)) {
         c5 += step2<5>(p0, w0, p1, w1, u0, u1);
-        if (u0) defer_word(win, i0, u0, wstart + (int64_t)i0, a, sh);
-        if (u1) defer_word(win, i1, u1, wstart + (int64_t)i1, a, sh);
+        SV_DEFER(i0, u0)
+        SV_DEFER(i1, u1)
       }
     }
   } else
@@ -676,10 +691,12 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
     c4 += step2<4>(p0, w0, p1, w1, u0, u1);
     if (__any_sync(0xFFFFFFFFu, u0 | u1)) {
       c5 += step2<5>(p0, w0, p1, w1, u0, u1);
-      if (u0) defer_word(win, i0, u0, aw0, a, sh);
-      if (u1) defer_word(win, i1, u1, aw1, a, sh);
+      SV_DEFER(i0, u0)
+      SV_DEFER(i1, u1)
     }
   }
+#undef SV_DEFER
+  if (pend_u) finish_word(win, pend_i, pend_u, wstart + (int64_t)pend_i, a, sh);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
@@ -732,6 +749,21 @@ __device__ __forceinline__ void scan_tile(const uint32_t *win, const TileArgs &a
   }
 }
 
+// Warp 0 copies a tile's buffered list entries to list positions
+// [base, base + n) of the range (positions >= cap are counted, not stored).
+__device__ __forceinline__ void copy_list(const TileArgs &a, const ScanShared &sh, unsigned long long base,
+                                          uint64_t off, uint64_t cap, uint32_t n) {
+  const uint32_t lane = threadIdx.x & 31u;
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  for (uint32_t e = lane; e < n; e += 32u) {
+    const unsigned long long idx = base + e;
+    if (idx < cap) {
+      a.list_n[off + idx] = sh.lst_n[e];
+      a.list_k[off + idx] = sh.lst_k[e];
+    }
+  }
+}
+
 // The tile queue hands out chunks of consecutive tiles, so that one CTA works
 // a range's tiles in order and the primes' offsets carry from one window to
 // the next; the last 4 tiles per CTA go one at a time, which keeps the CTAs'
@@ -778,9 +810,13 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
   }
   build_stamp_tables<NS>(stab);
   const uint32_t T = 32u * g.tw;  // a window starts T bits above the previous one
+  // warp 0: the previous tile's buffered list entries, not yet copied out
+  uint32_t lst_pending = 0;
+  unsigned long long lst_base = 0;
+  uint64_t lst_off = 0, lst_cap = 0;
   if (tid == 0) {
     sh.n_strag = 0;
-    sh.defer_n = 0;
+    sh.lst_cnt = 0;
     sh.req_idx = 0xFFFFFFFFu;
     uint32_t cs, ce;
     chunk_range((uint32_t)atomicAdd(&a.hdr->work_counter, 1ull), total, gridDim.x, &cs, &ce);
@@ -901,6 +937,11 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     const uint32_t bv0 = tid < g.bucket_cap ? bd[tid] : 0u;
     const uint32_t bv1 = tid + S < g.bucket_cap ? bd[tid + S] : 0u;
     stamp_window<NS>(win, stab, nz, nwords, wstart);
+    if (warp == 0) {  // the previous tile's list entries
+      if (lst_pending) copy_list(a, sh, lst_base, lst_off, lst_cap, lst_pending);
+      lst_pending = 0;
+      if (lane == 0) sh.lst_cnt = 0;
+    }
     if (tid == 0) {
       uint32_t need = 0;
       for (uint32_t k = 1; k <= kfirst; ++k)
@@ -1000,15 +1041,6 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       sh.chunk_end = next_end;
     }
     __syncthreads();
-    if (LEAN) {
-      // words that were still unresolved after k = 5
-      const uint32_t nq = min(sh.defer_n, kDeferCap);
-      for (uint32_t e = tid; e < nq; e += S) {
-        const uint32_t i = sh.defer_i[e];
-        finish_word(win, i, sh.defer_u[e], wstart + (int64_t)i, a, sh);
-      }
-      __syncthreads();
-    }
 
     // ---- 4. tile aggregates into the range's slot (warp 0) ------------------
     if (warp == 0) {
@@ -1033,14 +1065,20 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       sh.hist[lane + 32] = 0ull;
       sh.first[lane] = kNoN;
       sh.first[lane + 32] = kNoN;
-      __syncwarp();
-      if (lane == 0) {
-        sh.n_strag = 0;
-        sh.defer_n = 0;
+      // the buffered list entries: their place in the list now (the atomic's
+      // result is awaited only when they are copied, during the next tile)
+      lst_pending = min(sh.lst_cnt, kLstCap);
+      if (lst_pending) {
+        if (lane == 0) lst_base = atomicAdd(&slot->list_count, (unsigned long long)lst_pending);
+        lst_off = R.list_off;
+        lst_cap = R.list_cap;
       }
+      __syncwarp();
+      if (lane == 0) sh.n_strag = 0;
       __syncwarp();
     }
   }
+  if (warp == 0 && lst_pending) copy_list(a, sh, lst_base, lst_off, lst_cap, lst_pending);
 }
 
 // The stamped-prime counts instantiated (sv_config.stamp_primes).
