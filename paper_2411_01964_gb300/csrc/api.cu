@@ -132,6 +132,12 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   while (i < c->n_primes && i < g.i_med + (uint32_t)kMaxDensePrimes && (uint64_t)c->h_p[i] * c->h_p[i] <= dense_q)
     ++i;
   g.i_dense = i;
+  // head: at least one strike per thread and window (struck with a stride of
+  // one thread block); the rest of the dense primes share a numbering
+  const uint64_t head_q = 32ull * ((uint64_t)g.tw + g.mw) / (uint64_t)k.threads;
+  uint32_t h = g.i_med;
+  while (h < g.i_dense && (uint64_t)c->h_p[h] * c->h_p[h] <= head_q) ++h;
+  g.n_head = h - g.i_med;
   uint64_t lp = k.large_prime_min;
   if (span_bits) lp = std::max<uint64_t>(lp, host_isqrt(span_bits / 64) + 1);
   uint32_t il = primes_upto(c, lp - 1);

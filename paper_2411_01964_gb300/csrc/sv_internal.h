@@ -96,7 +96,8 @@ struct Geometry {
   uint32_t kwin;      // largest k decided inside a window (= margin_log2)
   uint32_t rec_t;     // record threshold T
   uint32_t i_med;     // first prime index struck per tile (after the stamped ones)
-  uint32_t i_dense;   // primes [i_med, i_dense) are struck warp-cooperatively
+  uint32_t i_dense;   // primes [i_med, i_dense) are struck cooperatively by all threads
+  uint32_t n_head;    // the first n_head of them hit a window at least once per thread
   uint32_t i_large;   // primes >= i_large come through buckets
   uint32_t bucket_cap;
   uint32_t tw_log2;   // log2(tw)

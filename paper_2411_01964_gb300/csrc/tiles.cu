@@ -10,9 +10,10 @@
 //              owner, not loaded; NS = sv_config.stamp_primes);
 //   2. strike: the next primes up to large_prime_min clear their odd multiples of
 //              p^2 with shared-memory atomicAnd: "dense" primes (>= 2 hits
-//              per window, at most 128 primes) have their strikes numbered and
-//              split evenly over all threads of the CTA, sparser ones take
-//              one thread per prime; larger primes
+//              per window, at most 128 primes) are struck by all threads of
+//              the CTA (the smallest with a stride of one block, the others
+//              through a common numbering of their strikes split evenly),
+//              sparser ones take one thread per prime; larger primes
 //              arrive as precomputed bit offsets in the tile's bucket
 //              (bucket_fill_kernel);
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
@@ -953,8 +954,17 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     // ---- 2. strikes: dense primes spread over all threads, sparse primes one
     //         thread each, large primes from the tile's bucket ---------------
     {
-      // dense primes: thread tid takes the strike numbers [X tid / S, X (tid+1) / S);
-      // the prime d of a number only moves forward
+      // head primes (>= 1 strike per thread): thread tid strikes their bits
+      // off + q (tid + S m)
+      const uint32_t nh = min(g.n_head, nd);
+      for (uint32_t d = 0; d < nh; ++d) {
+        const uint32_t q = sh.dense_q[d];
+        const uint32_t step = S * q;  // <= the window's bits
+        for (uint32_t b = sh.dense_off[d] + tid * q; b < nbits; b += step) strike(win, b);
+      }
+      // the other dense primes: thread tid takes the strike numbers
+      // [X0 + Xt tid / S, X0 + Xt (tid+1) / S) of their common numbering; the
+      // prime d of a number only moves forward
       const uint32_t g1 = sh.dense_grp[0], g2 = g1 + sh.dense_grp[1], g3 = g2 + sh.dense_grp[2];
       const uint32_t X = g3 + sh.dense_grp[3];
       auto pre = [&](uint32_t d) -> uint32_t {
@@ -962,10 +972,11 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
         const uint32_t gs = d >> 5;
         return sh.dense_pre[d] + (gs == 0 ? 0u : gs == 1 ? g1 : gs == 2 ? g2 : g3);
       };
-      uint32_t x = (X * tid) / S;  // X * S < 2^32: at most ~2^15 strikes per window
-      const uint32_t x1 = (X * (tid + 1u)) / S;
+      const uint32_t X0 = pre(nh), Xt = X - X0;  // Xt * S < 2^32: at most ~2^15 strikes per window
+      uint32_t x = X0 + (Xt * tid) / S;
+      const uint32_t x1 = X0 + (Xt * (tid + 1u)) / S;
       if (x < x1) {
-        uint32_t lo = 0, hi = nd;  // the largest d with pre(d) <= x: pre(lo) <= x < pre(hi)
+        uint32_t lo = nh, hi = nd;  // the largest d with pre(d) <= x: pre(lo) <= x < pre(hi)
         while (hi - lo > 1) {
           const uint32_t mid = (lo + hi) >> 1;
           if (pre(mid) <= x) lo = mid; else hi = mid;
