@@ -382,6 +382,7 @@ def main() -> int:
     total_ms = sum(step_ms)
     tile_ms, tile_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["tile"])
     bucket_ms, bucket_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["bucket_fill"])
+    other_ms = {k: B.sv_kernel_time(v.ctx, B.KERNEL_IDS[k]) for k in ("init", "stragglers", "list_compact")}
     B.sv_kernel_timing(v.ctx, False)
     res = v.fetch_range()
     assert sum(res.hist) + res.fail_len == n_odd
@@ -440,7 +441,8 @@ def main() -> int:
                 "d2h_bytes_per_step": d2h // max(e2e_steps, 1)},
         "gpu_launches": launches,
         "kernels": {"tile_ms_per_step": tile_ms / max(tile_n, 1),
-                    "bucket_fill_ms_per_step": bucket_ms / max(bucket_n, 1) if bucket_n else 0.0},
+                    "bucket_fill_ms_per_step": bucket_ms / max(bucket_n, 1) if bucket_n else 0.0,
+                    **{f"{k}_ms_per_step": (ms / max(cnt, 1) if cnt else 0.0) for k, (ms, cnt) in other_ms.items()}},
         "clocks": clk,
         "result": {"hist": res.hist[1:16], "kmax": res.kmax, "failures": res.fail_len,
                    "list_len": res.list_len},

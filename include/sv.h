@@ -78,6 +78,10 @@ typedef struct sv_config {
     uint64_t list_capacity;      /* device list entries per range (grown on overflow) */
     uint64_t device_mem_budget;  /* bytes the serving loop may hold for requests in flight */
     void *cuda_stream;           /* cudaStream_t used for all work; NULL = a library stream */
+    uint32_t list_stage_capacity;/* listed n a tile may stage for the ordered list (1..128; 0 = 128).
+                                    A tile with more repeats the launch through the unordered list
+                                    path; results never depend on it (small values exercise that path) */
+    uint32_t reserved0;
 } sv_config;
 
 /*
@@ -298,7 +302,7 @@ uint64_t sv_kernel_launches(const sv_ctx *ctx);
 /* Per-kernel timing: when enabled, every kernel launch is bracketed by CUDA
  * events recorded on the stream it is launched on.  enable != 0 turns it on,
  * 0 off; both reset the totals.  Kernel ids: 0 init, 1 bucket fill, 2 tile
- * (sieve + scan), 3 stragglers, 4 points. */
+ * (sieve + scan), 3 stragglers, 4 points, 5 ordered-list compaction. */
 sv_status sv_kernel_timing(sv_ctx *ctx, int enable);
 
 /* Total milliseconds and launch count of one kernel id since the last reset

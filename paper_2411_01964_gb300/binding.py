@@ -29,7 +29,7 @@ class sv_config(ctypes.Structure):
     _fields_ = [("tile_log2", u32), ("margin_log2", u32), ("threads", u32), ("large_prime_min", u32),
                 ("bucket_capacity", u32), ("record_k_threshold", u32), ("ctas_per_sm", u32),
                 ("stamp_primes", u32), ("list_capacity", u64), ("device_mem_budget", u64),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("list_stage_capacity", u32), ("reserved0", u32)]
 
 
 class sv_range_result(ctypes.Structure):
@@ -245,7 +245,7 @@ def sv_kernel_launches(ctx) -> int:
     return int(load().sv_kernel_launches(ctx))
 
 
-KERNEL_IDS = {"init": 0, "bucket_fill": 1, "tile": 2, "stragglers": 3, "points": 4}
+KERNEL_IDS = {"init": 0, "bucket_fill": 1, "tile": 2, "stragglers": 3, "points": 4, "list_compact": 5}
 
 
 def sv_kernel_timing(ctx, enable: bool) -> None:

@@ -158,6 +158,7 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   g.bucket_auto = cap;
   if (k.bucket_capacity) cap = k.bucket_capacity;  // explicit override (grown on overflow)
   g.bucket_cap = cap;
+  g.stage_cap = k.list_stage_capacity ? std::min<uint32_t>(k.list_stage_capacity, kStageCap) : kStageCap;
   return g;
 }
 
@@ -245,11 +246,22 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   ws.fail_total = fail_total;
   ws.j_max = j_max;
   ws.any_per_n = any_per_n;
+  ws.ordered = !any_per_n && g.rec_t > 5 && !ws.force_general;
   return SV_OK;
 }
 
+// Tile kernel mode of the planned launch: 0 lean with ordered lists, 1
+// general, 2 general with the per-n output.
+int launch_mode(const Workspace &ws) { return ws.any_per_n ? 2 : (ws.ordered ? 0 : 1); }
+
+// Ordered lists: one staging slot of kStageCap entries per tile.
+bool ensure_stage(Workspace &ws) {
+  const size_t t = ws.total_tiles ? ws.total_tiles : 1;
+  return !(ws.stage_n.ensure(t * kStageCap) || ws.stage_k.ensure(t * kStageCap) || ws.stage_cnt.ensure(t));
+}
+
 // Kernel ids of the per-kernel timing.
-enum { kKInit = 0, kKBucket = 1, kKTiles = 2, kKStrag = 3, kKPoints = 4 };
+enum { kKInit = 0, kKBucket = 1, kKTiles = 2, kKStrag = 3, kKPoints = 4, kKCompact = 5 };
 
 cudaEvent_t pool_event(sv_ctx *c) {
   if (!c->ev_pool.empty()) {
@@ -292,6 +304,8 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
       ws.strag.ensure(ws.strag_cap) || ws.bucket_count.ensure(ws.total_tiles ? ws.total_tiles : 1) ||
       ws.bucket_data.ensure((size_t)(ws.total_tiles ? ws.total_tiles : 1) * g.bucket_cap))
     return SV_ENOMEM;
+  const int mode = launch_mode(ws);
+  if (mode == 0 && !ensure_stage(ws)) return SV_ENOMEM;
   ws.bucket_cap = g.bucket_cap;
   SV_TRY_CUDA(cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * n, cudaMemcpyHostToDevice, st));
   SV_TRY_CUDA(cudaMemcpyAsync(ws.hdr.p, ws.h_hdr.p, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st));
@@ -300,7 +314,8 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
   SV_TRY_CUDA(cudaEventRecord(ws.staged, st));
   {
     KTimer kt(c, kKInit, st);
-    SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, ws.total_tiles, st));
+    SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, mode == 0 ? ws.stage_cnt.p : nullptr,
+                            ws.total_tiles, st));
     kt.done();
   }
   c->launches++;
@@ -332,13 +347,17 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     t.strag_cap = ws.strag_cap;
     t.bucket_count = ws.bucket_count.p;
     t.bucket_data = ws.bucket_data.p;
+    if (mode == 0) {
+      t.stage_n = ws.stage_n.p;
+      t.stage_k = ws.stage_k.p;
+      t.stage_cnt = ws.stage_cnt.p;
+    }
     const size_t smem = 4ull * (g.tw + g.mw);
     uint32_t grid = (uint32_t)c->num_sms * c->cfg.ctas_per_sm;
     if (grid > ws.total_tiles) grid = ws.total_tiles;
     {
       KTimer kt(c, kKTiles, st);
-      const int mode = ws.any_per_n ? 2 : (g.rec_t <= 5 ? 1 : 0);
-    SV_TRY_CUDA(launch_tiles(t, c->cfg.threads, grid, smem, mode, st));
+      SV_TRY_CUDA(launch_tiles(t, c->cfg.threads, grid, smem, mode, st));
       kt.done();
     }
     c->launches++;
@@ -353,12 +372,35 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     s.strag = ws.strag.p;
     s.strag_cap = ws.strag_cap;
     s.rec_t = g.rec_t;
+    if (mode == 0) {
+      s.stage_n = ws.stage_n.p;
+      s.stage_k = ws.stage_k.p;
+      s.stage_cnt = ws.stage_cnt.p;
+      s.stage_cap = g.stage_cap;
+      s.tw_log2 = g.tw_log2;
+    }
     {
       KTimer kt(c, kKStrag, st);
       SV_TRY_CUDA(launch_stragglers(s, (uint32_t)c->num_sms * 2, st));
       kt.done();
     }
     c->launches++;
+    if (mode == 0) {
+      CompactArgs ca{};
+      ca.reqs = ws.reqs.p;
+      ca.hdr = ws.hdr.p;
+      ca.slots = ws.slots.p;
+      ca.list_n = ws.list_n.p;
+      ca.list_k = ws.list_k.p;
+      ca.stage_n = ws.stage_n.p;
+      ca.stage_k = ws.stage_k.p;
+      ca.stage_cnt = ws.stage_cnt.p;
+      ca.stage_cap = g.stage_cap;
+      KTimer kt(c, kKCompact, st);
+      SV_TRY_CUDA(launch_compact(ca, std::min<uint32_t>((ws.total_tiles + 1023) / 1024, (uint32_t)c->num_sms), st));
+      kt.done();
+      c->launches++;
+    }
   }
   return SV_OK;
 }
@@ -375,14 +417,16 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       ws.strag.ensure(ws.strag_cap) || ws.bucket_count.ensure(ws.total_tiles ? ws.total_tiles : 1) ||
       ws.bucket_data.ensure((size_t)(ws.total_tiles ? ws.total_tiles : 1) * g.bucket_cap))
     return SV_ENOMEM;
+  const int mode = launch_mode(ws);
+  if (mode == 0 && !ensure_stage(ws)) return SV_ENOMEM;
   ws.bucket_cap = g.bucket_cap;
-  const int mode = ws.any_per_n ? 2 : (g.rec_t <= 5 ? 1 : 0);
   const size_t req_copy = std::min(ws.h_reqs.cap, ws.reqs.cap);
   GraphKey key;
   std::memset(&key, 0, sizeof(key));
   const void *ptrs[] = {ws.reqs.p,    ws.hdr.p,   ws.slots.p,        ws.list_n.p,       ws.list_k.p,
                         ws.fail_n.p,  ws.strag.p, ws.bucket_count.p, ws.bucket_data.p, ws.h_reqs.p,
-                        ws.h_hdr.p,   c->d_p,     (const void *)st};
+                        ws.h_hdr.p,   c->d_p,     (const void *)st,  ws.stage_n.p,      ws.stage_k.p,
+                        ws.stage_cnt.p};
   std::memcpy(key.p, ptrs, sizeof(ptrs));
   key.g = g;
   key.threads = c->cfg.threads;
@@ -398,7 +442,8 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
     const PrimeTab pt = prime_tab(c);
     cudaError_t e = cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * req_copy, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(ws.hdr.p, ws.h_hdr.p, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st);
-    if (!e) e = launch_init(ws.hdr.p, ws.slots.p, 1u << 20, ws.bucket_count.p, 1u << 20, st);
+    if (!e) e = launch_init(ws.hdr.p, ws.slots.p, 1u << 20, ws.bucket_count.p, mode == 0 ? ws.stage_cnt.p : nullptr,
+                            1u << 20, st);
     if (!e && pt.n > g.i_large) {
       BucketArgs b{};
       b.pt = pt;
@@ -423,6 +468,11 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       t.strag_cap = ws.strag_cap;
       t.bucket_count = ws.bucket_count.p;
       t.bucket_data = ws.bucket_data.p;
+      if (mode == 0) {
+        t.stage_n = ws.stage_n.p;
+        t.stage_k = ws.stage_k.p;
+        t.stage_cnt = ws.stage_cnt.p;
+      }
       e = launch_tiles(t, c->cfg.threads, (uint32_t)c->num_sms * c->cfg.ctas_per_sm, 4ull * (g.tw + g.mw), mode, st);
     }
     if (!e) {
@@ -437,7 +487,27 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       sa.strag = ws.strag.p;
       sa.strag_cap = ws.strag_cap;
       sa.rec_t = g.rec_t;
+      if (mode == 0) {
+        sa.stage_n = ws.stage_n.p;
+        sa.stage_k = ws.stage_k.p;
+        sa.stage_cnt = ws.stage_cnt.p;
+        sa.stage_cap = g.stage_cap;
+        sa.tw_log2 = g.tw_log2;
+      }
       e = launch_stragglers(sa, (uint32_t)c->num_sms * 2, st);
+    }
+    if (!e && mode == 0) {
+      CompactArgs ca{};
+      ca.reqs = ws.reqs.p;
+      ca.hdr = ws.hdr.p;
+      ca.slots = ws.slots.p;
+      ca.list_n = ws.list_n.p;
+      ca.list_k = ws.list_k.p;
+      ca.stage_n = ws.stage_n.p;
+      ca.stage_k = ws.stage_k.p;
+      ca.stage_cnt = ws.stage_cnt.p;
+      ca.stage_cap = g.stage_cap;
+      e = launch_compact(ca, (uint32_t)c->num_sms, st);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
@@ -457,7 +527,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
   // the graph reads the staging when it runs: the next plan waits for it
   if (!ws.staged && cudaEventCreateWithFlags(&ws.staged, cudaEventDisableTiming) != cudaSuccess) return SV_ECUDA;
   SV_TRY_CUDA(cudaEventRecord(ws.staged, st));
-  c->launches += 4;
+  c->launches += mode == 0 ? 5 : 4;
   ws.h2d_bytes = sizeof(ReqDesc) * req_copy + sizeof(LaunchHeader);
   return SV_OK;
 }
@@ -489,7 +559,13 @@ void sort_by_n(const uint64_t *ns, const uint8_t *ks, uint64_t cnt, uint64_t lo,
       for (uint32_t x = i; x > start[b] && out[x - 1].first > out[x].first; --x) std::swap(out[x - 1], out[x]);
 }
 
-enum Collect { kDone, kRetryBucket, kRetryStrag, kRetryList };
+enum Collect { kDone, kRetryBucket, kRetryStrag, kRetryList, kRetryGeneral };
+
+// How many list entries the consumer of range r can take: its result buffer,
+// the device region, or (a serving chunk) its request's buffer.
+uint64_t list_want(const RangeSpec &sp, const sv_range_result *o) {
+  return std::max(std::max(sp.list_cap, sp.want_cap), o ? o->list_cap : 0);
+}
 constexpr uint64_t kListRetryMax = 1ull << 26;  // larger lists are returned truncated, unordered
 
 // Waits for the launch, checks the device status word and copies results out.
@@ -511,12 +587,19 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
     *what = kRetryStrag;
     return SV_OK;
   }
-  // lists that the device truncated must be re-run with exact room, so that
-  // the caller receives the smallest entries, deterministically
+  if (status & kStListStage) {
+    *what = kRetryGeneral;
+    return SV_OK;
+  }
+  // an unordered list that the device truncated is re-run with exact room,
+  // so that the caller receives the smallest entries, deterministically; an
+  // ordered list already holds the smallest ones and is re-run only when
+  // the consumer can hold more than the device region did
   for (uint32_t r = 0; r < n; ++r) {
     const ResultSlot &s = ws.h_slots.p[r];
-    if (outs && outs[r] && outs[r]->list_cap && s.list_count > specs[r].list_cap &&
-        specs[r].list_cap < kListRetryMax) {
+    if (!outs || !outs[r]) continue;
+    const uint64_t limit = ws.ordered ? std::min<uint64_t>(list_want(specs[r], outs[r]), kListRetryMax) : kListRetryMax;
+    if (outs[r]->list_cap && s.list_count > specs[r].list_cap && specs[r].list_cap < limit) {
       *what = kRetryList;
       return SV_OK;
     }
@@ -569,11 +652,16 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
     const ReqDesc &d = ws.h_reqs.p[r];
     const uint64_t nl = std::min<uint64_t>(s.list_count, d.list_cap);
     if (nl && (o->list || o->list_k)) {
-      sort_by_n(ws.h_list_n.p + d.list_off, ws.h_list_k.p + d.list_off, nl, sp.lo, sp.hi, v);
       const uint64_t m = std::min<uint64_t>(nl, o->list_cap);
-      for (uint64_t i = 0; i < m; ++i) {
-        if (o->list) o->list[i] = v[i].first;
-        if (o->list_k) o->list_k[i] = v[i].second;
+      if (ws.ordered) {  // ascending already (list_compact_kernel)
+        if (o->list) std::memcpy(o->list, ws.h_list_n.p + d.list_off, 8 * m);
+        if (o->list_k) std::memcpy(o->list_k, ws.h_list_k.p + d.list_off, m);
+      } else {
+        sort_by_n(ws.h_list_n.p + d.list_off, ws.h_list_k.p + d.list_off, nl, sp.lo, sp.hi, v);
+        for (uint64_t i = 0; i < m; ++i) {
+          if (o->list) o->list[i] = v[i].first;
+          if (o->list_k) o->list_k[i] = v[i].second;
+        }
       }
     }
     const uint64_t nf = std::min<uint64_t>(s.fail_count, d.fail_cap);
@@ -639,8 +727,10 @@ sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result *
     if (what == kDone) {
       c->last_h2d = ws.h2d_bytes;
       c->last_d2h = ws.d2h_bytes;
+      ws.force_general = false;
       return SV_OK;
     }
+    if (what == kRetryGeneral) ws.force_general = true;
     if (what == kRetryBucket) {
       g.bucket_cap = std::max<uint32_t>(g.bucket_cap * 4, g.bucket_auto);
       ws.bucket_cap = g.bucket_cap;
@@ -649,7 +739,11 @@ sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result *
     if (what == kRetryList) {
       for (uint32_t r = 0; r < specs.size(); ++r) {
         const uint64_t cnt = ws.h_slots.p[r].list_count;
-        if (outs && outs[r] && cnt > specs[r].list_cap) specs[r].list_cap = std::min<uint64_t>(cnt, kListRetryMax);
+        if (outs && outs[r] && cnt > specs[r].list_cap) {
+          uint64_t cap = std::min<uint64_t>(cnt, kListRetryMax);
+          if (ws.ordered) cap = std::min<uint64_t>(cap, list_want(specs[r], outs[r]));
+          specs[r].list_cap = cap;
+        }
       }
     }
   }
@@ -670,6 +764,8 @@ sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_rang
   Collect what;
   sv_status s = collect(c, specs, outs, ws, st, &what);
   *retry = (what != kDone);
+  if (what == kDone) ws.force_general = false;
+  if (what == kRetryGeneral) ws.force_general = true;
   if (what == kRetryBucket)
     ws.bucket_cap = std::max<uint32_t>(ws.bucket_cap * 4, make_geometry(c, max_span_bits(c, specs)).bucket_auto);
   if (what == kRetryStrag) ws.strag_cap *= 4;
@@ -951,6 +1047,7 @@ sv_status sv_fetch_batch(sv_ctx *c, sv_range_result *out, size_t count) {
     std::vector<RangeSpec> specs = c->pending_specs;
     if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
     if (what == kRetryStrag) c->ws.strag_cap *= 4;
+    if (what == kRetryGeneral) c->ws.force_general = true;
     s = run_ranges(c, specs, outs.data(), c->stream, c->ws, true);
   }
   return s;
@@ -1029,6 +1126,7 @@ sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
     std::vector<RangeSpec> specs = c->pending_specs;
     if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
     if (what == kRetryStrag) c->ws.strag_cap *= 4;
+    if (what == kRetryGeneral) c->ws.force_general = true;
     s = run_ranges(c, specs, outs, c->stream, c->ws, false);
     if (s) return s;
   }

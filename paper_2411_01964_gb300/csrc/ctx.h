@@ -49,6 +49,8 @@ struct RangeSpec {
   uint64_t lo = 0, hi = 0;
   uint8_t *d_per_n = nullptr;   // device per-n output or null
   uint64_t list_cap = 0;        // device list entries reserved for it
+  uint64_t want_cap = 0;        // entries the final consumer can hold (0: list_cap); an ordered
+                                // list truncated below it is repeated with more room
   uint64_t fail_cap = 0;
   bool sieve_only = false;
   uint32_t *bitmap_out = nullptr;
@@ -56,7 +58,7 @@ struct RangeSpec {
 
 // What a captured launch graph depends on (compared bytewise).
 struct GraphKey {
-  const void *p[13];
+  const void *p[16];
   Geometry g;
   uint32_t threads, ctas, mode, strag_cap;
   uint64_t req_copy;
@@ -81,6 +83,9 @@ struct Workspace {
   DBuf<uint32_t> bucket_count;
   DBuf<uint32_t> bucket_data;
   DBuf<uint8_t> per_n;
+  DBuf<uint64_t> stage_n;    // ordered lists: per-tile staged entries (kStageCap per tile)
+  DBuf<uint8_t> stage_k;
+  DBuf<uint32_t> stage_cnt;
   DBuf<uint64_t> points;
   DBuf<uint8_t> points_out;
   HBuf<uint64_t> h_points;
@@ -91,6 +96,8 @@ struct Workspace {
   uint32_t strag_cap = 1u << 16;
   uint32_t bucket_cap = 0;
   bool any_per_n = false;
+  bool ordered = false;        // the planned launch produces ordered lists (tile kernel mode 0)
+  bool force_general = false;  // repeat with the unordered list path (a tile's staging overflowed)
   uint64_t j_max = 0;  // largest odd-multiplier count of the launch (bucket fill by j)
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
   // the captured launch graph and what it was captured for

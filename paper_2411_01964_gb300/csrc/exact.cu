@@ -89,10 +89,27 @@ __global__ void __launch_bounds__(256) straggler_kernel(StragArgs a) {
         atomicAdd(&slot->hist[k], 1ull);
         atomicMin(&slot->first_n[k], (unsigned long long)st.n);
         if (k >= a.rec_t) {
-          const unsigned long long idx = atomicAdd(&slot->list_count, 1ull);
-          if (idx < R.list_cap) {
-            a.list_n[R.list_off + idx] = st.n;
-            a.list_k[R.list_off + idx] = (uint8_t)k;
+          if (a.stage_n) {
+            // ordered lists: join the staged entries of the tile holding n
+            const uint64_t t = ((((st.n - 1) >> 1) >> 5) - (uint64_t)R.w0) >> a.tw_log2;
+            if (t < R.n_tiles) {
+              const uint32_t gt = R.tile_base + (uint32_t)t;
+              const uint32_t e = atomicAdd(&a.stage_cnt[gt], 1u);
+              if (e < a.stage_cap) {
+                a.stage_n[(size_t)gt * kStageCap + e] = st.n;
+                a.stage_k[(size_t)gt * kStageCap + e] = (uint8_t)k;
+              } else {
+                atomicOr(&a.hdr->status, kStListStage);
+              }
+            } else {
+              atomicOr(&a.hdr->status, kStBadTile);
+            }
+          } else {
+            const unsigned long long idx = atomicAdd(&slot->list_count, 1ull);
+            if (idx < R.list_cap) {
+              a.list_n[R.list_off + idx] = st.n;
+              a.list_k[R.list_off + idx] = (uint8_t)k;
+            }
           }
         }
       } else {

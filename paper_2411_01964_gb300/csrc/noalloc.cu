@@ -226,7 +226,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
       return SV_ECUDA;
     // the array keeps the previous call's contents: the counters, the result
     // slot and the bucket counts are cleared on the device first
-    if (launch_init(d_hdr, d_slot, 1, d_bcount, d.n_tiles, st) != cudaSuccess) return SV_ECUDA;
+    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, st) != cudaSuccess) return SV_ECUDA;
     c->launches++;
     if (d.n_primes > g.i_large) {
       BucketArgs b{};
@@ -256,7 +256,9 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
     t.bucket_data = d_bdata;
     uint32_t grid = (uint32_t)c->num_sms * c->cfg.ctas_per_sm;
     if (grid > d.n_tiles) grid = d.n_tiles;
-    const int mode = g.rec_t <= 5 ? 1 : 0;
+    // the general scan mode: its list needs no per-tile staging, which the
+    // array has no room for; smallest_into picks the smallest entries
+    const int mode = 1;
     if (launch_tiles(t, c->cfg.threads, grid, 4ull * (g.tw + g.mw), mode, st) != cudaSuccess) return SV_ECUDA;
     c->launches++;
     StragArgs sa{};

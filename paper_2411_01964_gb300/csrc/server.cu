@@ -246,7 +246,7 @@ class Server {
     const uint64_t budget = c_->cfg.device_mem_budget;
     const uint64_t in_flight = mem_in_flight();
     auto launch_mem = [&](uint64_t t, uint64_t l, uint64_t np) {
-      return t * 4ull * (s.ws.bucket_cap ? s.ws.bucket_cap + 1 : 1024) + l * 9 + np * 17 +
+      return t * 4ull * (s.ws.bucket_cap ? s.ws.bucket_cap + 1 : 1024) + t * (9ull * kStageCap + 4) + l * 9 + np * 17 +
              (uint64_t)(s.items.size() + 1) * (sizeof(ReqDesc) + sizeof(ResultSlot)) + (1u << 20);
     };
     for (auto it = queue_.begin(); it != queue_.end();) {
@@ -263,6 +263,7 @@ class Server {
           sp.lo = clo;
           sp.hi = chi;
           sp.list_cap = lc;
+          sp.want_cap = r.r.result->list_cap;
           sp.fail_cap = 64;
           s.items.push_back({r.ticket, clo, chi});
           s.specs.push_back(sp);

@@ -22,7 +22,12 @@ enum : uint32_t {
   kStBucketOverflow = 1u << 0,  // a tile bucket was full: rerun with a larger one
   kStStragOverflow = 1u << 1,   // straggler queue full: rerun with a larger one
   kStBadTile = 1u << 2,         // a tile index failed a bounds check
+  kStListStage = 1u << 3,       // a tile's staged list was full: rerun with the unordered list path
 };
+
+// List entries (mink >= T) a tile stages for the ordered list (mode 0): the
+// tile kernel's shared buffer and the stride of the per-tile staging slots.
+constexpr uint32_t kStageCap = 128;
 
 // Resident table of the odd primes 3 <= p <= pmax (ascending), structure of
 // arrays.  mu[i] = floor((2^64-1) / p^2) is the Barrett (1986) constant for
@@ -104,6 +109,8 @@ struct Geometry {
   uint32_t bucket_auto;  // host only: the automatic capacity estimate
   uint32_t i_hyb;     // primes >= i_hyb reach the buckets by enumerating odd multipliers j
   uint32_t p_hyb;     // the prime at i_hyb (0xFFFFFFFF: none)
+  uint32_t stage_cap; // usable staged list entries per tile (<= kStageCap)
+  uint32_t pad;
 };
 
 struct TileArgs {
@@ -119,6 +126,10 @@ struct TileArgs {
   uint32_t strag_cap;
   const uint32_t *bucket_count;
   const uint32_t *bucket_data;
+  // mode 0: tile t stages its list entries at [t * kStageCap, + stage_cnt[t])
+  uint64_t *stage_n;
+  uint8_t *stage_k;
+  uint32_t *stage_cnt;
 };
 
 struct BucketArgs {
@@ -141,11 +152,33 @@ struct StragArgs {
   const Straggler *strag;
   uint32_t strag_cap;
   uint32_t rec_t;
+  // ordered lists (mode 0): a straggler's list entry joins its tile's staged entries
+  uint64_t *stage_n;    // null: append to the list directly
+  uint8_t *stage_k;
+  uint32_t *stage_cnt;
+  uint32_t stage_cap;
+  uint32_t tw_log2;
+};
+
+// The ordered list (mode 0): each range's staged entries, tile by tile and
+// ascending within a tile, into its list region; list_count = the total.
+struct CompactArgs {
+  const ReqDesc *reqs;
+  LaunchHeader *hdr;
+  ResultSlot *slots;
+  uint64_t *list_n;
+  uint8_t *list_k;
+  const uint64_t *stage_n;
+  const uint8_t *stage_k;
+  const uint32_t *stage_cnt;
+  uint32_t stage_cap;
+  uint32_t pad;
 };
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
-                        uint32_t *bucket_count, uint32_t n_tiles, cudaStream_t st);
+                        uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, cudaStream_t st);
+cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st);
 // j_max: the largest number of odd multipliers any range of the launch needs
 // for the primes >= p_hyb (sizes the enumeration grid).
 cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs, uint64_t j_max,

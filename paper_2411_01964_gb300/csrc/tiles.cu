@@ -162,13 +162,16 @@ __device__ __forceinline__ void strike(uint32_t *win, uint32_t b) {
 }
 
 // ---------------------------------------------------------------------------
-// init: zero the launch's counters, result slots and bucket counts.
+// init: zero the launch's counters, result slots, bucket and staged-list counts.
 // ---------------------------------------------------------------------------
-__global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count) {
+__global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count, uint32_t *stage_cnt) {
   const uint32_t n_slots = hdr->n_reqs, n_tiles = hdr->total_tiles;
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gs = gridDim.x * blockDim.x;
-  for (uint32_t i = gid; i < n_tiles; i += gs) bucket_count[i] = 0;
+  for (uint32_t i = gid; i < n_tiles; i += gs) {
+    bucket_count[i] = 0;
+    if (stage_cnt) stage_cnt[i] = 0;
+  }
   for (uint32_t i = gid; i < n_slots * (uint32_t)kMaxK; i += gs) {
     slots[i / kMaxK].hist[i % kMaxK] = 0ull;
     slots[i / kMaxK].first_n[i % kMaxK] = kNoN;
@@ -185,13 +188,13 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
 }
 
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
-                        uint32_t *bucket_count, uint32_t n_tiles, cudaStream_t st) {
+                        uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, cudaStream_t st) {
   uint64_t work = (uint64_t)n_slots * kMaxK;
   if (n_tiles > work) work = n_tiles;
   uint32_t grid = (uint32_t)((work + 255) / 256);
   if (grid < 1) grid = 1;
   if (grid > 1024) grid = 1024;
-  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count);
+  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt);
   return cudaGetLastError();
 }
 
@@ -404,7 +407,7 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
 // ---------------------------------------------------------------------------
 constexpr uint32_t kMaxDense = kMaxDensePrimes;  // dense primes per tile: four warps, one prime per lane
 
-constexpr uint32_t kLstCap = 128;  // list entries (mink >= T) buffered per tile
+constexpr uint32_t kLstCap = kStageCap;  // list entries (mink >= T) buffered per tile
 constexpr uint32_t kMaxSparse = kMaxSparsePrimes;  // primes struck one thread each, per tile
 
 struct ScanShared {
@@ -501,9 +504,25 @@ __device__ __forceinline__ void scan_step(uint32_t sf, uint32_t &unres, uint32_t
   if (!LEAN && (uint32_t)K >= rec_t && hit) list_append(a, sh.req, hit, 32ull * (uint64_t)aw, (uint32_t)K);
 }
 
+// Mode 0: list entries (n with mink = k >= T) go to the tile's shared
+// buffer, which the tile's flush stages for the ordered list.  Entries
+// beyond the buffer are only counted; the flush reports them (kStListStage)
+// and the launch is repeated with the unordered list path.
+__device__ __noinline__ void list_buffer(ScanShared &sh, uint32_t hit, uint64_t J0, uint32_t k) {
+  while (hit) {
+    const uint32_t b = __ffs(hit) - 1;
+    const uint32_t e = atomicAdd(&sh.lst_cnt, 1u);
+    if (e < kLstCap) {
+      sh.lst_n[e] = 2ull * (J0 + b) + 1ull;
+      sh.lst_k[e] = (uint8_t)k;
+    }
+    hit &= hit - 1;
+  }
+}
+
 // k = 6 .. kwin (rare): whole-word look-back reads; counts, first occurrences
 // below T and lists go straight to shared/global atomics.
-template <bool PER_N>
+template <bool LEAN, bool PER_N>
 __device__ __noinline__ uint32_t scan_tail(const uint32_t *win, uint32_t i, bool act, uint32_t unres,
                                            uint32_t pl[6], const TileArgs &a, ScanShared &sh, int64_t aw,
                                            uint32_t kwin, uint32_t rec_t) {
@@ -519,10 +538,12 @@ __device__ __noinline__ uint32_t scan_tail(const uint32_t *win, uint32_t i, bool
     }
     if (hit) {
       atomicAdd(&sh.hist[k], (unsigned long long)__popc(hit));
-      if (k < rec_t)
+      if (LEAN || k < rec_t)
         atomicMin(&sh.first[k], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(hit) - 1)) + 1ull));
-      else
-        list_append(a, sh.req, hit, J0, k);
+      if (k >= rec_t) {
+        if (LEAN) list_buffer(sh, hit, J0, k);
+        else list_append(a, sh.req, hit, J0, k);
+      }
     }
   }
   if (unres) straggler_push(a, sh, unres, J0, kwin + 1u);
@@ -574,7 +595,7 @@ __device__ __forceinline__ void scan_word(const uint32_t *win, uint32_t i, bool 
         SV_STEP(4, __funnelshift_l(wp, w, 8), c4)
         if (__any_sync(0xFFFFFFFFu, unres)) {
           SV_STEP(5, __funnelshift_l(wp, w, 16), c5)
-          if (__any_sync(0xFFFFFFFFu, unres)) scan_tail<PER_N>(win, i, act, unres, pl, a, sh, aw, kwin, rec_t);
+          if (__any_sync(0xFFFFFFFFu, unres)) scan_tail<LEAN, PER_N>(win, i, act, unres, pl, a, sh, aw, kwin, rec_t);
         }
       }
     }
@@ -583,23 +604,6 @@ __device__ __forceinline__ void scan_word(const uint32_t *win, uint32_t i, bool 
   if (PER_N && sh.req.per_n_k) write_per_n(sh.req.per_n_k, 32ull * (uint64_t)aw, sh.req.jlo, valid, pl);
 }
 
-// List entries (n with mink = k >= T) go to the tile's shared buffer; the
-// tile's flush reserves their place in the range's list with one atomic,
-// and they are copied out during the next tile's stamping.  Entries beyond
-// the buffer go straight to the list.
-__device__ __noinline__ void list_buffer(const TileArgs &a, ScanShared &sh, uint32_t hit, uint64_t J0, uint32_t k) {
-  while (hit) {
-    const uint32_t b = __ffs(hit) - 1;
-    const uint32_t e = atomicAdd(&sh.lst_cnt, 1u);
-    if (e < kLstCap) {
-      sh.lst_n[e] = 2ull * (J0 + b) + 1ull;
-      sh.lst_k[e] = (uint8_t)k;
-    } else {
-      list_append(a, sh.req, 1u << b, J0, k);
-    }
-    hit &= hit - 1;
-  }
-}
 
 // One thread finishes one word whose n (bits u) are unresolved after k = 5:
 // k = 6 .. kwin by whole-word look-back, then the exact test for the rest.
@@ -614,7 +618,7 @@ __device__ __noinline__ void finish_word(const uint32_t *win, uint32_t i, uint32
     if (h) {
       atomicAdd(&sh.hist[k], (unsigned long long)__popc(h));
       atomicMin(&sh.first[k], (unsigned long long)(2ull * (J0 + (uint64_t)(__ffs(h) - 1)) + 1ull));
-      if (k >= rec_t) list_buffer(a, sh, h, J0, k);
+      if (k >= rec_t) list_buffer(sh, h, J0, k);
     }
   }
   if (u) straggler_push(a, sh, u, J0, kwin + 1u);
@@ -750,21 +754,6 @@ __device__ __forceinline__ void scan_tile(const uint32_t *win, const TileArgs &a
   }
 }
 
-// Warp 0 copies a tile's buffered list entries to list positions
-// [base, base + n) of the range (positions >= cap are counted, not stored).
-__device__ __forceinline__ void copy_list(const TileArgs &a, const ScanShared &sh, unsigned long long base,
-                                          uint64_t off, uint64_t cap, uint32_t n) {
-  const uint32_t lane = threadIdx.x & 31u;
-  base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  for (uint32_t e = lane; e < n; e += 32u) {
-    const unsigned long long idx = base + e;
-    if (idx < cap) {
-      a.list_n[off + idx] = sh.lst_n[e];
-      a.list_k[off + idx] = sh.lst_k[e];
-    }
-  }
-}
-
 // The tile queue hands out chunks of consecutive tiles, so that one CTA works
 // a range's tiles in order and the primes' offsets carry from one window to
 // the next; the last 4 tiles per CTA go one at a time, which keeps the CTAs'
@@ -811,10 +800,6 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
   }
   build_stamp_tables<NS>(stab);
   const uint32_t T = 32u * g.tw;  // a window starts T bits above the previous one
-  // warp 0: the previous tile's buffered list entries, not yet copied out
-  uint32_t lst_pending = 0;
-  unsigned long long lst_base = 0;
-  uint64_t lst_off = 0, lst_cap = 0;
   if (tid == 0) {
     sh.n_strag = 0;
     sh.lst_cnt = 0;
@@ -938,11 +923,6 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     const uint32_t bv0 = tid < g.bucket_cap ? bd[tid] : 0u;
     const uint32_t bv1 = tid + S < g.bucket_cap ? bd[tid + S] : 0u;
     stamp_window<NS>(win, stab, nz, nwords, wstart);
-    if (warp == 0) {  // the previous tile's list entries
-      if (lst_pending) copy_list(a, sh, lst_base, lst_off, lst_cap, lst_pending);
-      lst_pending = 0;
-      if (lane == 0) sh.lst_cnt = 0;
-    }
     if (tid == 0) {
       uint32_t need = 0;
       for (uint32_t k = 1; k <= kfirst; ++k)
@@ -1076,20 +1056,127 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       sh.hist[lane + 32] = 0ull;
       sh.first[lane] = kNoN;
       sh.first[lane + 32] = kNoN;
-      // the buffered list entries: their place in the list now (the atomic's
-      // result is awaited only when they are copied, during the next tile)
-      lst_pending = min(sh.lst_cnt, kLstCap);
-      if (lst_pending) {
-        if (lane == 0) lst_base = atomicAdd(&slot->list_count, (unsigned long long)lst_pending);
-        lst_off = R.list_off;
-        lst_cap = R.list_cap;
+      // mode 0: the tile's list entries to its staging slot (ordered later)
+      if (LEAN) {
+        const uint32_t m = sh.lst_cnt, ms = min(m, g.stage_cap);
+        for (uint32_t e = lane; e < ms; e += 32u) {
+          a.stage_n[(size_t)gt * kStageCap + e] = sh.lst_n[e];
+          a.stage_k[(size_t)gt * kStageCap + e] = sh.lst_k[e];
+        }
+        if (lane == 0) {
+          if (ms) a.stage_cnt[gt] = ms;
+          if (m > ms) atomicOr(&a.hdr->status, kStListStage);
+        }
       }
       __syncwarp();
-      if (lane == 0) sh.n_strag = 0;
+      if (lane == 0) {
+        sh.n_strag = 0;
+        sh.lst_cnt = 0;
+      }
       __syncwarp();
     }
   }
-  if (warp == 0 && lst_pending) copy_list(a, sh, lst_base, lst_off, lst_cap, lst_pending);
+}
+
+// ---------------------------------------------------------------------------
+// The ordered list (mode 0).  The launch's tiles are cut into blocks of 1024,
+// one thread per tile; a tile's place in its range's list is the number of
+// entries its range staged in the tiles before it: the block's inclusive
+// scan (segmented at range starts) plus, for a range that began in an
+// earlier block, the sum of its staged counts there.  Each tile's few
+// entries arrive unordered and are ranked among themselves, so the list
+// comes out ascending.  Entries past the range's list capacity are counted,
+// not stored: the smallest ones are kept.  The thread of a range's last tile
+// writes the range's total.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kCompactBlock = 1024;
+
+__device__ __forceinline__ uint32_t range_of_tile(const ReqDesc *reqs, uint32_t n_reqs, uint32_t t) {
+  uint32_t lo = 0, hi = n_reqs;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (reqs[mid].tile_base <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kCompactBlock) list_compact_kernel(CompactArgs a) {
+  __shared__ uint32_t incl_s[kCompactBlock];
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t carry_s;
+  const uint32_t n_reqs = a.hdr->n_reqs, total = a.hdr->total_tiles;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const uint32_t nblk = (total + kCompactBlock - 1) / kCompactBlock;
+  for (uint32_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const uint32_t b0 = blk * kCompactBlock;
+    const uint32_t t = b0 + tid;
+    const bool act = t < total;
+    const uint32_t r = act ? range_of_tile(a.reqs, n_reqs, t) : 0u;
+    const ReqDesc *R = act ? &a.reqs[r] : nullptr;
+    const bool listed = act && !R->sieve_only && t - R->tile_base < R->n_tiles;
+    const uint32_t cnt = listed ? min(a.stage_cnt[t], a.stage_cap) : 0u;
+    // carry-in: the staged entries of the block's first range before the block
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    {
+      const uint32_t r0 = range_of_tile(a.reqs, n_reqs, b0);
+      const uint32_t tb0 = a.reqs[r0].tile_base;
+      uint32_t part = 0;
+      if (!a.reqs[r0].sieve_only)
+        for (uint32_t u = tb0 + tid; u < b0; u += kCompactBlock) part += min(a.stage_cnt[u], a.stage_cap);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+      if (lane == 0 && part) atomicAdd(&carry_s, part);
+    }
+    // inclusive block scan of the counts
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = wsum[lane];
+      uint32_t wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+        if (lane >= (uint32_t)o) wi += y;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    incl += wsum[warp];
+    incl_s[tid] = incl;
+    __syncthreads();
+    if (listed) {
+      // entries of this range in the block's tiles before t, plus the carry-in
+      const uint32_t s0 = R->tile_base > b0 ? R->tile_base - b0 : 0u;
+      uint64_t pos = (uint64_t)(incl - cnt) - (s0 ? incl_s[s0 - 1] : 0u);
+      if (R->tile_base < b0) pos += carry_s;
+      const uint64_t *sn = a.stage_n + (size_t)t * kStageCap;
+      const uint8_t *sk = a.stage_k + (size_t)t * kStageCap;
+      for (uint32_t e = 0; e < cnt; ++e) {
+        const uint64_t n = sn[e];
+        uint32_t rank = 0;
+        for (uint32_t f = 0; f < cnt; ++f) rank += sn[f] < n ? 1u : 0u;
+        if (pos + rank < R->list_cap) {
+          a.list_n[R->list_off + pos + rank] = n;
+          a.list_k[R->list_off + pos + rank] = sk[e];
+        }
+      }
+      if (t - R->tile_base == R->n_tiles - 1) a.slots[R->slot].list_count = pos + cnt;
+    }
+    __syncthreads();  // the shared arrays are reused by the next block
+  }
+}
+
+cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st) {
+  if (grid == 0) return cudaSuccess;
+  list_compact_kernel<<<grid, kCompactBlock, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 // The stamped-prime counts instantiated (sv_config.stamp_primes).

@@ -106,6 +106,8 @@ def test_knobs_do_not_change_results(orc, knobs):
             g = v.verify_range(lo, hi, per_n=True)
             o = orc.verify_range(lo, hi, per_n=True, list_k_threshold=v.config.record_k_threshold)
             assert_same_range(g, o)
+            # without the per-n output (T >= 6: the lean scan and the ordered list)
+            assert_same_range(v.verify_range(lo, hi), o, per_n=False)
 
 
 def test_small_buckets_overflow_and_retry(orc):
@@ -114,6 +116,19 @@ def test_small_buckets_overflow_and_retry(orc):
         lo, hi = (1 << 50) - (1 << 23), 1 << 50
         g = v.verify_range(lo, hi, per_n=True)
         assert_same_range(g, orc.verify_range(lo, hi, per_n=True))
+
+
+@pytest.mark.parametrize("stage_cap", [1, 2, 0])
+def test_ordered_list_and_its_fallback(orc, stage_cap):
+    # lists come out of the device ascending (staged per tile, compacted);
+    # a tile with more listed n than it may stage repeats the launch through
+    # the unordered list path, with the same results
+    with Verifier(max_hi=(1 << 50) + (1 << 24), tile_log2=16, list_stage_capacity=stage_cap) as v:
+        for lo, hi in [(3, 1 << 22), ((1 << 40) + 7, (1 << 40) + 7 + (1 << 23) + 99)]:
+            o = orc.verify_range(lo, hi)
+            assert_same_range(v.verify_range(lo, hi), o, per_n=False)
+            g = v.verify_range(lo, hi, list_cap=7)
+            assert g.list_len == len(o.list_n) and np.array_equal(g.list_n, o.list_n[:7])
 
 
 def test_list_capacity_truncation_is_deterministic(gpu, orc):
