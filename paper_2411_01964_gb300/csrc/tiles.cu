@@ -235,6 +235,46 @@ __device__ __forceinline__ void bucket_emit(const BucketArgs &a, uint64_t J, int
   }
 }
 
+// One struck bit's bucket entries, computed before their slots are reserved:
+// the tile whose core holds it and, if it also lies in the next tile's
+// look-back, that tile (t1 = 0xFFFFFFFF: none).
+struct BucketHit {
+  uint32_t t0, off0, t1, off1, i0, i1;
+};
+__device__ __forceinline__ BucketHit bucket_hit(const BucketArgs &a, uint64_t J, int64_t w0, uint32_t tile_base,
+                                                uint32_t n_tiles) {
+  BucketHit h;
+  const int64_t w = (int64_t)(J >> 5);
+  uint32_t t = 0;
+  if (w >= w0) t = (uint32_t)((uint64_t)(w - w0) >> a.g.tw_log2);
+  if (t >= n_tiles) t = n_tiles - 1;  // cannot happen: J < E
+  const int64_t wst = w0 + (int64_t)t * a.g.tw - (int64_t)a.g.mw;
+  h.t0 = tile_base + t;
+  h.off0 = (uint32_t)((int64_t)J - 32 * wst);
+  h.t1 = 0xFFFFFFFFu;
+  h.off1 = 0;
+  if (t + 1 < n_tiles) {
+    const int64_t wst1 = wst + (int64_t)a.g.tw;
+    if (w >= wst1) {
+      h.t1 = tile_base + t + 1;
+      h.off1 = (uint32_t)((int64_t)J - 32 * wst1);
+    }
+  }
+  return h;
+}
+__device__ __forceinline__ void bucket_reserve(const BucketArgs &a, BucketHit &h) {
+  h.i0 = atomicAdd(&a.bucket_count[h.t0], 1u);
+  h.i1 = h.t1 != 0xFFFFFFFFu ? atomicAdd(&a.bucket_count[h.t1], 1u) : 0u;
+}
+__device__ __forceinline__ void bucket_store(const BucketArgs &a, const BucketHit &h) {
+  if (h.i0 < a.g.bucket_cap) a.bucket_data[(size_t)h.t0 * a.g.bucket_cap + h.i0] = h.off0;
+  else atomicOr(&a.hdr->status, kStBucketOverflow);
+  if (h.t1 != 0xFFFFFFFFu) {
+    if (h.i1 < a.g.bucket_cap) a.bucket_data[(size_t)h.t1 * a.g.bucket_cap + h.i1] = h.off1;
+    else atomicOr(&a.hdr->status, kStBucketOverflow);
+  }
+}
+
 // Primes i_large <= i < i_hyb: one thread per prime, one Barrett reduction
 // per range for its first struck bit, then every further hit.
 __global__ void __launch_bounds__(256) bucket_fill_kernel(BucketArgs a) {
@@ -276,7 +316,24 @@ __global__ void __launch_bounds__(256) bucket_fill_kernel(BucketArgs a) {
       for (uint32_t r = 0; r < nr; ++r) {
         const FillReq f = s_req[r];
         if (pi >= f.n_primes || f.n_tiles == 0 || f.E <= f.A) continue;
-        for (uint64_t J = f.A + first_strike(f.A, q, mu); J < f.E; J += q) bucket_emit(a, J, f.w0, f.tile_base, f.n_tiles);
+        uint64_t J = f.A + first_strike(f.A, q, mu);
+        // four hits at a time: their slot reservations go out together, so
+        // the atomics' round trips overlap instead of queueing one by one
+        for (; J + 3 * q < f.E; J += 4 * q) {
+          BucketHit h0 = bucket_hit(a, J, f.w0, f.tile_base, f.n_tiles);
+          BucketHit h1 = bucket_hit(a, J + q, f.w0, f.tile_base, f.n_tiles);
+          BucketHit h2 = bucket_hit(a, J + 2 * q, f.w0, f.tile_base, f.n_tiles);
+          BucketHit h3 = bucket_hit(a, J + 3 * q, f.w0, f.tile_base, f.n_tiles);
+          bucket_reserve(a, h0);
+          bucket_reserve(a, h1);
+          bucket_reserve(a, h2);
+          bucket_reserve(a, h3);
+          bucket_store(a, h0);
+          bucket_store(a, h1);
+          bucket_store(a, h2);
+          bucket_store(a, h3);
+        }
+        for (; J < f.E; J += q) bucket_emit(a, J, f.w0, f.tile_base, f.n_tiles);
       }
     }
   }
