@@ -10,10 +10,10 @@
 //              owner, not loaded; NS = sv_config.stamp_primes);
 //   2. strike: the next primes up to large_prime_min clear their odd multiples of
 //              p^2 with shared-memory atomicAnd: "dense" primes (>= 2 hits
-//              per window, at most 128 primes) are struck by all threads of
-//              the CTA (the smallest with a stride of one block, the others
-//              through a common numbering of their strikes split evenly),
-//              sparser ones take one thread per prime; larger primes
+//              per window, at most 128 primes) are struck cooperatively (the
+//              smallest by the whole CTA with a stride of one block, the
+//              others by one warp each with a stride of one warp), sparser
+//              ones take one thread per prime; larger primes
 //              arrive as precomputed bit offsets in the tile's bucket
 //              (bucket_fill_kernel);
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
@@ -479,15 +479,10 @@ struct ScanShared {
   uint32_t n_strag;                // stragglers this tile sent to the exact test
   uint32_t need;                   // k <= 5 whose first occurrence this tile may still improve
   uint32_t lst_cnt;                // list entries this tile found (buffered up to kLstCap)
-  // the dense primes' strikes of this tile, numbered consecutively prime by
-  // prime: prime d owns numbers [pre(d), pre(d+1)), its strike number x is
-  // bit dense_off[d] + (x - pre(d)) * dense_q[d].  pre(d) = dense_pre[d] (the
-  // exclusive prefix within d's group of 32) + the strikes of groups < d/32
-  // (dense_grp[g] = strikes of group g).
+  // the dense primes of this tile: q = p^2 and the window offset of the
+  // first struck bit (carried from window to window)
   uint32_t dense_q[kMaxDense];
   uint32_t dense_off[kMaxDense];
-  uint32_t dense_pre[kMaxDense];
-  uint32_t dense_grp[kMaxDense / 32];
   uint32_t dense_tq[kMaxDense];    // (32 tw) mod dense_q: a window's shift, reduced
   unsigned long long lst_n[kLstCap];  // the buffered list entries: n and mink
   uint8_t lst_k[kLstCap];
@@ -933,8 +928,8 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     // ---- 1. stamp the smallest primes; the dense primes' first strikes -------
     if (warp < kMaxDense / 32) {  // blockDim.x >= 128: warps 0..3 exist
       const uint32_t d = 32u * warp + lane;
-      uint32_t q = 1, off = 0, cnt = 0;
       if (d < nd) {
+        uint32_t q, off;
         if (fresh) {
           const uint64_t p = a.pt.p[g.i_med + d];
           q = (uint32_t)(p * p);
@@ -947,20 +942,9 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
           if (off >= q) off -= q;
           if (off >= q) off %= q;  // only after a window that began below bit 0
         }
-        cnt = off < nbits ? (nbits - off + q - 1) / q : 0u;
-      }
-      uint32_t incl = cnt;  // inclusive prefix within the group of 32
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-      }
-      if (d < nd) {
         sh.dense_q[d] = q;
         sh.dense_off[d] = off;
-        sh.dense_pre[d] = incl - cnt;
       }
-      if (lane == 31) sh.dense_grp[warp] = incl;  // lanes with d >= nd add nothing
     }
     const uint32_t nz = (wstart < 0) ? (uint32_t)min((int64_t)nwords, -wstart) : 0u;
     for (uint32_t i = tid; i < nz; i += S) win[i] = 0u;  // integers below 1
@@ -999,35 +983,15 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
         const uint32_t step = S * q;  // <= the window's bits
         for (uint32_t b = sh.dense_off[d] + tid * q; b < nbits; b += step) strike(win, b);
       }
-      // the other dense primes: thread tid takes the strike numbers
-      // [X0 + Xt tid / S, X0 + Xt (tid+1) / S) of their common numbering; the
-      // prime d of a number only moves forward
-      const uint32_t g1 = sh.dense_grp[0], g2 = g1 + sh.dense_grp[1], g3 = g2 + sh.dense_grp[2];
-      const uint32_t X = g3 + sh.dense_grp[3];
-      auto pre = [&](uint32_t d) -> uint32_t {
-        if (d >= nd) return X;
-        const uint32_t gs = d >> 5;
-        return sh.dense_pre[d] + (gs == 0 ? 0u : gs == 1 ? g1 : gs == 2 ? g2 : g3);
-      };
-      const uint32_t X0 = pre(nh), Xt = X - X0;  // Xt * S < 2^32: at most ~2^15 strikes per window
-      uint32_t x = X0 + (Xt * tid) / S;
-      const uint32_t x1 = X0 + (Xt * (tid + 1u)) / S;
-      if (x < x1) {
-        uint32_t lo = nh, hi = nd;  // the largest d with pre(d) <= x: pre(lo) <= x < pre(hi)
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (pre(mid) <= x) lo = mid; else hi = mid;
-        }
-        uint32_t d = lo, p0 = pre(d), pn = pre(d + 1), q = sh.dense_q[d], off = sh.dense_off[d];
-        for (; x < x1; ++x) {
-          while (x >= pn) {
-            ++d;
-            p0 = pn;
-            pn = pre(d + 1);
-            q = sh.dense_q[d];
-            off = sh.dense_off[d];
-          }
-          strike(win, off + (x - p0) * q);
+      // the other dense primes, one warp each in a snake order over the warps
+      // (their strike counts fall with p); lane l strikes off + q (l + 32 m)
+      {
+        const uint32_t nw = S >> 5;
+        for (uint32_t rd = 0;; ++rd) {
+          const uint32_t d = nh + rd * nw + ((rd & 1u) ? nw - 1u - warp : warp);
+          if (d >= nd) break;
+          const uint32_t q = sh.dense_q[d], step = 32u * q;  // step <= the window's bits
+          for (uint32_t b = sh.dense_off[d] + lane * q; b < nbits; b += step) strike(win, b);
         }
       }
       // a full window's strikes carry to the next window: its first struck
