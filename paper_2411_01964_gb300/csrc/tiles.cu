@@ -366,7 +366,7 @@ __device__ __forceinline__ void emit_word(const BucketArgs &a, const ReqDesc &R,
   }
 }
 
-constexpr uint64_t kWarpJ = 32;  // odd j < 2 kWarpJ are handled warp-cooperatively
+constexpr uint64_t kWarpJ = 32;  // odd j < 2 kWarpJ are handled cooperatively (warp or grid)
 
 // Bitmap bits [b0, b1] ((p-1)/2) of the odd p >= ph, p <= p_top, with an odd
 // multiple j p^2 in [mlo, mhi]; false if there are none.
@@ -383,6 +383,7 @@ __device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t 
 }
 
 __global__ void __launch_bounds__(256) bucket_fill_j_kernel(BucketArgs a) {
+  __shared__ uint64_t s_iv[kWarpJ][2];  // bitmap bits [b0, b1] of the small multipliers' p intervals
   const uint32_t n_reqs = a.hdr->n_reqs;
   const Geometry g = a.g;
   if (a.hdr->max_primes <= g.i_hyb) return;
@@ -398,21 +399,51 @@ __global__ void __launch_bounds__(256) bucket_fill_j_kernel(BucketArgs a) {
     const uint64_t jmax = mhi / ph2;
     const uint64_t p_top = a.pt.p[R.n_primes - 1];  // primes with p^2 < hi
     // the smallest multipliers have the longest p intervals (and the most
-    // hits): one warp per j for j < 2 kWarpJ, lanes striding over the words
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint64_t wpb = blockDim.x >> 5;
-    for (uint64_t t = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < kWarpJ && 2 * t + 1 <= jmax;
-         t += (uint64_t)gridDim.x * wpb) {
-      const uint64_t j = 2 * t + 1;
-      uint64_t b0, b1;
-      if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
-      uint64_t w_last = b1 >> 5;
-      if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
-      for (uint64_t w = (b0 >> 5) + lane; w <= w_last; w += 32) {
-        uint32_t mm = a.pt.bits[w];
-        if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
-        if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
-        emit_word(a, R, mm, w, j);
+    // hits).  A long range (>= 2^30 odd numbers) spreads their bitmap words
+    // over all the x-threads of the grid, j by j, with the intervals computed
+    // once per block; a shorter one gives each small j to one warp, lanes
+    // striding over words.
+    const bool spread = E - A >= (1ull << 30);
+    if (spread) {
+      __syncthreads();  // s_iv is reused for every range
+      if (threadIdx.x < kWarpJ) {
+        const uint64_t j = 2 * threadIdx.x + 1;
+        uint64_t b0 = 1, b1 = 0;
+        if (j > jmax || !p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) b0 = 1, b1 = 0;
+        s_iv[threadIdx.x][0] = b0;
+        s_iv[threadIdx.x][1] = b1;
+      }
+      __syncthreads();
+      const uint64_t gx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nx = (uint64_t)gridDim.x * blockDim.x;
+      for (uint32_t t = 0; t < kWarpJ; ++t) {
+        const uint64_t b0 = s_iv[t][0], b1 = s_iv[t][1];
+        if (b1 < b0) continue;
+        const uint64_t j = 2 * t + 1;
+        uint64_t w_last = b1 >> 5;
+        if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
+        for (uint64_t w = (b0 >> 5) + gx; w <= w_last; w += nx) {
+          uint32_t mm = a.pt.bits[w];
+          if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
+          if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
+          emit_word(a, R, mm, w, j);
+        }
+      }
+    } else {
+      const uint32_t lane = threadIdx.x & 31u;
+      const uint64_t wpb = blockDim.x >> 5;
+      for (uint64_t t = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < kWarpJ && 2 * t + 1 <= jmax;
+           t += (uint64_t)gridDim.x * wpb) {
+        const uint64_t j = 2 * t + 1;
+        uint64_t b0, b1;
+        if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+        uint64_t w_last = b1 >> 5;
+        if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
+        for (uint64_t w = (b0 >> 5) + lane; w <= w_last; w += 32) {
+          uint32_t mm = a.pt.bits[w];
+          if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
+          if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
+          emit_word(a, R, mm, w, j);
+        }
       }
     }
     // the rest: one thread per j
