@@ -49,7 +49,8 @@ class RangeResult:
 
 
 class _ResultBuffers:
-    """Host buffers wired into an sv_range_result."""
+    """Host buffers wired into an sv_range_result (fresh per call: the result
+    keeps views of them)."""
 
     def __init__(self, list_cap: int, fail_cap: int, n_per_n: int | None):
         self.res = B.sv_range_result()
@@ -75,9 +76,9 @@ class _ResultBuffers:
             pn = self.per_n[: r.n_odd]
         return RangeResult(lo=r.lo, hi=r.hi, n_odd=r.n_odd, hist=[int(x) for x in r.hist],
                            first_n=[int(x) for x in r.first_n], ksum=r.ksum, kmax=r.kmax,
-                           list_n=self.list_n[:nl].copy(), list_k=self.list_k[:nl].copy(),
+                           list_n=self.list_n[:nl], list_k=self.list_k[:nl],
                            list_len=r.list_len, list_overflow=bool(r.list_overflow),
-                           failures=self.fails[:nf].copy(), fail_len=r.fail_len, per_n_k=pn)
+                           failures=self.fails[:nf], fail_len=r.fail_len, per_n_k=pn)
 
 
 def odd_count(lo: int, hi: int) -> int:

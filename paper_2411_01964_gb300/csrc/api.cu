@@ -976,7 +976,8 @@ sv_status sv_verify_range(sv_ctx *c, uint64_t lo, uint64_t hi, sv_range_result *
     specs[0].d_per_n = c->ws.per_n.p;
   }
   sv_range_result *outs[1] = {out};
-  s = run_ranges(c, specs, outs, c->stream, c->ws, false);
+  // the launch as the captured graph (replayed while the sizes fit)
+  s = run_ranges(c, specs, outs, c->stream, c->ws, true);
   if (s) return s;
   if (out->per_n_k && n_odd) {
     if (cudaMemcpyAsync(out->per_n_k, c->ws.per_n.p, n_odd, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
