@@ -75,10 +75,27 @@ class SweepTotals:
         return None if v == NO_N else v
 
     def summary(self) -> dict:
-        return {"lo": self.lo, "hi": self.hi, "chunks": self.chunks, "n_odd": self.n_odd,
-                "hist": {k: c for k, c in enumerate(self.hist) if c}, "ksum": self.ksum, "kmax": self.kmax,
-                "failures": self.fail_count,
-                "records": {m: self.record(m) for m in range(1, self.kmax) if self.record(m) is not None}}
+        out = {"lo": self.lo, "hi": self.hi, "chunks": self.chunks, "n_odd": self.n_odd,
+               "hist": {k: c for k, c in enumerate(self.hist) if c}, "ksum": self.ksum, "kmax": self.kmax,
+               "failures": self.fail_count,
+               "records": {m: self.record(m) for m in range(1, self.kmax) if self.record(m) is not None}}
+        if self.n_odd:
+            out["heuristic"] = heuristic_check(self)
+        return out
+
+
+def heuristic_check(tot: SweepTotals, z_flag: float = 6.0) -> dict:
+    """The swept counts against the heuristic of Sec. 2: per k the expected
+    count and binomial deviation over the swept odd n, the sum of the
+    exponents against its expectation (Sec. 4), and every k whose count
+    lies more than z_flag deviations away."""
+    from . import heuristics
+    dev = heuristics.deviations(tot.hist, tot.n_odd)
+    E, sig = heuristics.expected_sum(2 * tot.n_odd)  # S/2 odd n below S
+    return {"expected": {k: round(e, 1) for k, _, e, _, _ in dev if e >= 0.05},
+            "z": {k: round(z, 3) for k, _, e, _, z in dev if e >= 0.05},
+            "ksum_expected": round(float(E)), "ksum_z": float((tot.ksum - E) / sig),
+            "flagged": [k for k, _, e, _, z in dev if z > z_flag]}
 
 
 def chunk_bounds(lo: int, hi: int, chunk_log2: int) -> list[tuple[int, int]]:
