@@ -110,6 +110,15 @@ def test_knobs_do_not_change_results(orc, knobs):
             assert_same_range(v.verify_range(lo, hi), o, per_n=False)
 
 
+@pytest.mark.parametrize("lo,hi", [((1 << 53) - (1 << 22) - 11, (1 << 53) + 5),
+                                   ((1 << 56) + 12345, (1 << 56) + 12345 + (1 << 21) + 77)])
+def test_ranges_above_2p50(orc, lo, hi):
+    # beyond the paper's sweep: prime tables past 2^25 (2^28 at 2^56)
+    with Verifier(max_hi=hi + 1) as v:
+        assert_same_range(v.verify_range(lo, hi, per_n=True), orc.verify_range(lo, hi, per_n=True))
+        assert_same_range(v.verify_range(lo, hi), orc.verify_range(lo, hi), per_n=False)
+
+
 def test_small_buckets_overflow_and_retry(orc):
     # a bucket capacity far too small must be detected on the device and grown
     with Verifier(max_hi=1 << 51, tile_log2=18, large_prime_min=40, bucket_capacity=1) as v:
