@@ -442,8 +442,10 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
     const PrimeTab pt = prime_tab(c);
     cudaError_t e = cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * req_copy, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(ws.hdr.p, ws.h_hdr.p, sizeof(LaunchHeader), cudaMemcpyHostToDevice, st);
-    if (!e) e = launch_init(ws.hdr.p, ws.slots.p, 1u << 20, ws.bucket_count.p, mode == 0 ? ws.stage_cnt.p : nullptr,
-                            1u << 20, st);
+    // sized for the buffers (the kernel reads the launch's sizes from the header)
+    if (!e) e = launch_init(ws.hdr.p, ws.slots.p, (uint32_t)std::min<size_t>(ws.slots.cap, 1u << 20), ws.bucket_count.p,
+                            mode == 0 ? ws.stage_cnt.p : nullptr, (uint32_t)std::min<size_t>(ws.bucket_count.cap, 1u << 30),
+                            st);
     if (!e && pt.n > g.i_large) {
       BucketArgs b{};
       b.pt = pt;

@@ -1142,6 +1142,7 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
 // writes the range's total.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kCompactBlock = 1024;
+constexpr uint32_t kRankRegs = 8;  // staged entries of a tile ranked in registers (more: from memory)
 
 __device__ __forceinline__ uint32_t range_of_tile(const ReqDesc *reqs, uint32_t n_reqs, uint32_t t) {
   uint32_t lo = 0, hi = n_reqs;
@@ -1152,7 +1153,7 @@ __device__ __forceinline__ uint32_t range_of_tile(const ReqDesc *reqs, uint32_t 
   return lo;
 }
 
-__global__ void __launch_bounds__(kCompactBlock) list_compact_kernel(CompactArgs a) {
+__global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactArgs a) {
   __shared__ uint32_t incl_s[kCompactBlock];
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t carry_s;
@@ -1210,13 +1211,31 @@ __global__ void __launch_bounds__(kCompactBlock) list_compact_kernel(CompactArgs
       if (R->tile_base < b0) pos += carry_s;
       const uint64_t *sn = a.stage_n + (size_t)t * kStageCap;
       const uint8_t *sk = a.stage_k + (size_t)t * kStageCap;
-      for (uint32_t e = 0; e < cnt; ++e) {
-        const uint64_t n = sn[e];
-        uint32_t rank = 0;
-        for (uint32_t f = 0; f < cnt; ++f) rank += sn[f] < n ? 1u : 0u;
-        if (pos + rank < R->list_cap) {
-          a.list_n[R->list_off + pos + rank] = n;
-          a.list_k[R->list_off + pos + rank] = sk[e];
+      if (cnt <= kRankRegs) {
+        // the usual case: a few entries, ranked in registers
+        uint64_t v[kRankRegs];
+#pragma unroll
+        for (uint32_t e = 0; e < kRankRegs; ++e) v[e] = e < cnt ? sn[e] : ~0ull;
+#pragma unroll
+        for (uint32_t e = 0; e < kRankRegs; ++e) {
+          if (e >= cnt) break;
+          uint32_t rank = 0;
+#pragma unroll
+          for (uint32_t f = 0; f < kRankRegs; ++f) rank += v[f] < v[e] ? 1u : 0u;
+          if (pos + rank < R->list_cap) {
+            a.list_n[R->list_off + pos + rank] = v[e];
+            a.list_k[R->list_off + pos + rank] = sk[e];
+          }
+        }
+      } else {
+        for (uint32_t e = 0; e < cnt; ++e) {
+          const uint64_t n = sn[e];
+          uint32_t rank = 0;
+          for (uint32_t f = 0; f < cnt; ++f) rank += sn[f] < n ? 1u : 0u;
+          if (pos + rank < R->list_cap) {
+            a.list_n[R->list_off + pos + rank] = n;
+            a.list_k[R->list_off + pos + rank] = sk[e];
+          }
         }
       }
       if (t - R->tile_base == R->n_tiles - 1) a.slots[R->slot].list_count = pos + cnt;
