@@ -1,31 +1,37 @@
 // tiles.cu -- the range path: Algorithm 1 (sieve) and Algorithm 2 (search
 // for the smallest k) of Sec. 3, fused per shared-memory tile.
 //
-// One persistent CTA per SM pulls tiles from a device work queue.  A tile is
-// 2^tile_log2 consecutive odd numbers of one range plus a look-back margin of
-// mw words below it (the paper keeps the preceding interval for the same
-// purpose, Sec. 3 after Algorithm 2).  Per tile:
+// Persistent CTAs (two per SM by default) take chunks of consecutive tiles
+// from a device work counter.  A tile is 2^tile_log2 consecutive odd numbers
+// of one range plus a look-back margin of mw words below it (the paper keeps
+// the preceding interval for the same purpose, Sec. 3 after Algorithm 2).
+// Per tile:
 //   1. stamp:  every window word starts as the AND of the periodic strike
-//              patterns of the NS smallest odd primes (computed by the word's
-//              owner, not loaded; NS = sv_config.stamp_primes);
-//   2. strike: the next primes up to large_prime_min clear their odd multiples of
-//              p^2 with shared-memory atomicAnd: "dense" primes (>= 2 hits
-//              per window, at most 128 primes) are struck cooperatively (the
-//              smallest by the whole CTA with a stride of one block, the
-//              others by one warp each with a stride of one warp), sparser
-//              ones take one thread per prime; larger primes
-//              arrive as precomputed bit offsets in the tile's bucket
-//              (bucket_fill_kernel);
+//              patterns of the NS smallest odd primes, read from two small
+//              shared-memory tables indexed by the word number modulo the
+//              product of their squares (NS = sv_config.stamp_primes);
+//   2. strike: the next primes up to the bucket threshold clear their odd
+//              multiples of p^2 with shared-memory atomicAnd.  "Dense" primes
+//              (>= 2 hits per window, at most 128) are struck cooperatively:
+//              the smallest by the whole CTA with a stride of one block, the
+//              others by one warp each with a stride of one warp.  Sparser
+//              ones take one thread per prime.  The offsets of both carry
+//              from a window to the next one of the same range.  Larger
+//              primes arrive as precomputed bit offsets in the tile's bucket
+//              (bucket_fill_kernel, bucket_fill_j_kernel);
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
 //              flags of n - 2^k are word i shifted by 2^(k-1) bits: a funnel
 //              shift of (w[i-1], w[i]) for k <= 5, the word w[i - 2^(k-6)] for
-//              6 <= k <= kwin.  unresolved &= ~flags; hist[k] += popc(newly);
-//              the warp stops at the first k where no lane has an unresolved
-//              n.  n still unresolved after kwin go to the exact straggler
-//              test.  Each warp records its first occurrence of each frequent
-//              exponent by ballot until it has seen them all;
+//              6 <= k <= kwin.  unresolved &= ~flags; hist[k] += popc(newly).
+//              k = 1..4 run without votes (two words per lane); a word still
+//              unresolved after k = 5 is finished by its lane after the loop;
+//              n still unresolved after kwin go to the exact straggler test.
+//              Tiles that may hold a range's first occurrence of some k <= 5
+//              record it by ballot;
 //   4. reduce: per-tile histogram and first occurrences into the range's
-//              result slot (Sec. 3 "Collecting the results").
+//              result slot (Sec. 3 "Collecting the results"), and the tile's
+//              listed n (mink >= T) into its staging slot for the ordered
+//              list (list_compact_kernel).
 // The bitmap never leaves shared memory.
 #include <cuda_runtime.h>
 
