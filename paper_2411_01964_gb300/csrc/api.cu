@@ -562,6 +562,7 @@ void sort_by_n(const uint64_t *ns, const uint8_t *ks, uint64_t cnt, uint64_t lo,
 }
 
 enum Collect { kDone, kRetryBucket, kRetryStrag, kRetryList, kRetryGeneral };
+constexpr uint64_t kSpeculativeList = 1ull << 18;  // list entries copied without waiting for the count
 
 // How many list entries the consumer of range r can take: its result buffer,
 // the device region, or (a serving chunk) its request's buffer.
@@ -577,8 +578,22 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
   *what = kDone;
   SV_TRY_CUDA(cudaMemcpyAsync(ws.h_hdr.p, ws.hdr.p, sizeof(LaunchHeader), cudaMemcpyDeviceToHost, st));
   SV_TRY_CUDA(cudaMemcpyAsync(ws.h_slots.p, ws.slots.p, sizeof(ResultSlot) * n, cudaMemcpyDeviceToHost, st));
+  // an ordered list region is copied with the header (one wait instead of
+  // two) when it is small enough to copy whole
+  uint64_t spec_end = 0;
+  if (ws.ordered && outs) {
+    for (uint32_t r = 0; r < n; ++r)
+      if (outs[r] && (outs[r]->list || outs[r]->list_k))
+        spec_end = std::max<uint64_t>(spec_end, ws.h_reqs.p[r].list_off + ws.h_reqs.p[r].list_cap);
+    if (spec_end > kSpeculativeList) spec_end = 0;
+  }
+  if (spec_end) {
+    if (ws.h_list_n.ensure(spec_end) || ws.h_list_k.ensure(spec_end)) return SV_ENOMEM;
+    SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_n.p, ws.list_n.p, 8 * spec_end, cudaMemcpyDeviceToHost, st));
+    SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_k.p, ws.list_k.p, spec_end, cudaMemcpyDeviceToHost, st));
+  }
   SV_TRY_CUDA(cudaStreamSynchronize(st));
-  uint64_t d2h = sizeof(LaunchHeader) + sizeof(ResultSlot) * n;
+  uint64_t d2h = sizeof(LaunchHeader) + sizeof(ResultSlot) * n + 9 * spec_end;
   const uint32_t status = ws.h_hdr.p->status;
   if (status & kStBadTile) return SV_ECUDA;
   if (status & kStBucketOverflow) {
@@ -617,8 +632,9 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
     if (nl && (outs[r]->list || outs[r]->list_k)) list_end = std::max<uint64_t>(list_end, d.list_off + nl);
     if (nf && outs[r]->failures) fail_end = std::max<uint64_t>(fail_end, d.fail_off + nf);
   }
+  if (list_end <= spec_end) list_end = 0;  // already here
   if (list_end || fail_end) {
-    if (ws.h_list_n.ensure(list_end ? list_end : 1) || ws.h_list_k.ensure(list_end ? list_end : 1) ||
+    if ((list_end && (ws.h_list_n.ensure(list_end) || ws.h_list_k.ensure(list_end))) ||
         ws.h_fail_n.ensure(fail_end ? fail_end : 1))
       return SV_ENOMEM;
     if (list_end) {
