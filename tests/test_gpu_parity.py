@@ -161,6 +161,17 @@ def test_points(gpu, orc):
     assert list(g[:12]) == [m + 1 for m in sorted(want)]
 
 
+def test_points_above_2p50(orc):
+    # the exact path with prime tables past 2^25: random points up to 2^57
+    # and CRT-forced points with mink >= 9 (Remark in Sec. 2)
+    pts = inputs.random_points(4, 40, 1 << 50, 1 << 57) + inputs.crt_forced(8, 12, seed=9, max_bits=57)
+    with Verifier(max_hi=(1 << 57) + 1) as v:
+        g = v.min_k(pts)
+    o = orc.min_k(pts)
+    assert np.array_equal(g, o)
+    assert all(int(k) >= 9 for k in g[40:])
+
+
 def test_points_device_entry(gpu, orc):
     import torch
     pts = inputs.random_points(9, 257, 2, 1 << 46)
