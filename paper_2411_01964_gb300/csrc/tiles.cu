@@ -12,7 +12,7 @@
 //              product of their squares (NS = sv_config.stamp_primes);
 //   2. strike: the next primes up to the bucket threshold clear their odd
 //              multiples of p^2 with shared-memory atomicAnd.  "Dense" primes
-//              (>= 2 hits per window, at most 128) are struck cooperatively:
+//              (>= 4 hits per window, at most 128) are struck cooperatively:
 //              the smallest by the whole CTA with a stride of one block, the
 //              others by one warp each with a stride of one warp.  Sparser
 //              ones take one thread per prime.  The offsets of both carry
@@ -848,7 +848,7 @@ __device__ __forceinline__ void scan_tile(const uint32_t *win, const TileArgs &a
 // the next; the last 4 tiles per CTA go one at a time, which keeps the CTAs'
 // finishing times within about one tile of each other.  Chunk j is tiles
 // [*s, *e).
-constexpr uint32_t kChunk = 8;
+constexpr uint32_t kChunk = 12;
 __device__ __forceinline__ void chunk_range(uint32_t j, uint32_t total, uint32_t ctas, uint32_t *s, uint32_t *e) {
   const uint32_t reserve = 4u * ctas;
   const uint32_t n_big = total > reserve ? (total - reserve) / kChunk : 0u;
