@@ -299,10 +299,12 @@ sv_status sv_verify_range_noalloc(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_rang
 /* Number of kernels this context has launched so far. */
 uint64_t sv_kernel_launches(const sv_ctx *ctx);
 
-/* Per-kernel timing: when enabled, every kernel launch is bracketed by CUDA
- * events recorded on the stream it is launched on.  enable != 0 turns it on,
- * 0 off; both reset the totals.  Kernel ids: 0 init, 1 bucket fill, 2 tile
- * (sieve + scan), 3 stragglers, 4 points, 5 ordered-list compaction. */
+/* Per-kernel timing: when enabled, each launch of a timed kernel is
+ * bracketed by CUDA events recorded on the stream it is launched on (launches
+ * replayed from a captured graph are not timed).  enable: 0 off, -1 every
+ * kernel, otherwise a bit mask of kernel ids (bit i: id i); every call resets
+ * the totals.  Kernel ids: 0 init, 1 bucket fill, 2 tile (sieve + scan),
+ * 3 stragglers, 4 points, 5 ordered-list compaction. */
 sv_status sv_kernel_timing(sv_ctx *ctx, int enable);
 
 /* Total milliseconds and launch count of one kernel id since the last reset

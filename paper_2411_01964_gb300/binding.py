@@ -248,8 +248,17 @@ def sv_kernel_launches(ctx) -> int:
 KERNEL_IDS = {"init": 0, "bucket_fill": 1, "tile": 2, "stragglers": 3, "points": 4, "list_compact": 5}
 
 
-def sv_kernel_timing(ctx, enable: bool) -> None:
-    check(load().sv_kernel_timing(ctx, 1 if enable else 0), "sv_kernel_timing")
+def sv_kernel_timing(ctx, enable) -> None:
+    """enable: False (off), True (every kernel), or an iterable of KERNEL_IDS names."""
+    if enable is True:
+        arg = -1
+    elif not enable:
+        arg = 0
+    else:
+        arg = 0
+        for name in enable:
+            arg |= 1 << KERNEL_IDS[name]
+    check(load().sv_kernel_timing(ctx, arg), "sv_kernel_timing")
 
 
 def sv_kernel_time(ctx, kernel: int) -> tuple[float, int]:

@@ -260,6 +260,9 @@ bool ensure_stage(Workspace &ws) {
   return !(ws.stage_n.ensure(t * kStageCap) || ws.stage_k.ensure(t * kStageCap) || ws.stage_cnt.ensure(t));
 }
 
+// Blocks of the bucket fill: one full wave.
+uint32_t fill_blocks(const sv_ctx *c) { return (uint32_t)c->num_sms * kFillBlocksPerSm; }
+
 // Kernel ids of the per-kernel timing.
 enum { kKInit = 0, kKBucket = 1, kKTiles = 2, kKStrag = 3, kKPoints = 4, kKCompact = 5 };
 
@@ -281,7 +284,7 @@ struct KTimer {
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   KTimer(sv_ctx *c_, int id_, cudaStream_t st_) : c(c_), id(id_), st(st_) {
-    if (c->kprof && st == c->stream) {  // the serving thread's streams are never timed
+    if (((c->kprof >> id) & 1u) && st == c->stream) {  // the serving thread's streams are never timed
       a = pool_event(c);
       cudaEventRecord(a, st);
     }
@@ -329,7 +332,7 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     b.bucket_count = ws.bucket_count.p;
     b.bucket_data = ws.bucket_data.p;
     KTimer kt(c, kKBucket, st);
-    SV_TRY_CUDA(launch_bucket_fill(b, ws.max_primes - g.i_large, n, ws.j_max, st));
+    SV_TRY_CUDA(launch_bucket_fill(b, ws.max_primes - g.i_large, n, ws.j_max, fill_blocks(c), st));
     kt.done();
     c->launches++;
   }
@@ -454,7 +457,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       b.hdr = ws.hdr.p;
       b.bucket_count = ws.bucket_count.p;
       b.bucket_data = ws.bucket_data.p;
-      e = launch_bucket_fill(b, pt.n - g.i_large, 1u << 20, 1ull << 23, st);
+      e = launch_bucket_fill(b, pt.n - g.i_large, 1u << 20, 1ull << 23, fill_blocks(c), st);
     }
     if (!e) {
       TileArgs t{};
@@ -1183,7 +1186,7 @@ sv_status sv_kernel_timing(sv_ctx *c, int enable) {
     c->k_ms[i] = 0.0;
     c->k_n[i] = 0;
   }
-  c->kprof = enable != 0;
+  c->kprof = enable == -1 ? 0xFFFFFFFFu : (uint32_t)enable;
   return SV_OK;
 }
 

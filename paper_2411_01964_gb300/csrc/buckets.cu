@@ -1,0 +1,308 @@
+// buckets.cu -- the large primes' strikes, computed ahead of the tiles (the
+// bucket part of Algorithm 1, Sec. 3).  For every prime above the tiles' own
+// strike range and every range of the launch, each struck bit of the range's
+// windows is appended to the bucket of the tile whose core holds it, and to
+// the next tile's bucket when it also lies in that tile's look-back margin.
+//
+// One launch does both kinds of large primes, as work items taken by a
+// block-stride loop, so that the two run side by side:
+//   * Barrett items (prime block, request chunk): primes i_large <= i < i_hyb,
+//     one thread per prime; one Barrett reduction per range gives its first
+//     struck bit, then the thread walks the further hits;
+//   * multiplier items (slice, request): primes p >= p_hyb, reached through
+//     their odd multipliers j (j p^2 in the range) and the prime bitmap.
+// A bucket slot is reserved with a global atomic that returns the slot; a
+// Barrett thread reserves the slots of up to four hits together, so that
+// their round trips overlap instead of queueing one behind the other.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "strike.h"
+#include "sv_internal.h"
+
+namespace sv {
+
+constexpr uint32_t kFillThreads = 256;
+constexpr uint32_t kFillReqChunk = 64;  // ranges per Barrett item
+constexpr uint32_t kHitBatch = 4;       // slot reservations in flight per thread
+constexpr uint64_t kWarpJ = 32;         // odd j < 2 kWarpJ are handled cooperatively (warp or grid)
+
+struct FillReq {
+  uint64_t A, E;  // struck bits wanted: [A, E)
+  int64_t w0;
+  uint32_t tile_base, n_tiles, n_primes, pad;
+};
+
+// One struck bit's bucket entries, computed before their slots are reserved:
+// the tile whose core holds it and, if it also lies in the next tile's
+// look-back, that tile (t1 = 0xFFFFFFFF: none).
+struct BucketHit {
+  uint32_t t0, off0, t1, off1, i0, i1;
+};
+
+__device__ __forceinline__ BucketHit bucket_hit(const BucketArgs &a, uint64_t J, int64_t w0, uint32_t tile_base,
+                                                uint32_t n_tiles) {
+  BucketHit h;
+  const int64_t w = (int64_t)(J >> 5);
+  uint32_t t = 0;
+  if (w >= w0) t = (uint32_t)((uint64_t)(w - w0) >> a.g.tw_log2);
+  if (t >= n_tiles) t = n_tiles - 1;  // cannot happen: J < E
+  const int64_t wst = w0 + (int64_t)t * a.g.tw - (int64_t)a.g.mw;
+  h.t0 = tile_base + t;
+  h.off0 = (uint32_t)((int64_t)J - 32 * wst);
+  h.t1 = 0xFFFFFFFFu;
+  h.off1 = 0;
+  h.i0 = h.i1 = 0;
+  if (t + 1 < n_tiles) {
+    const int64_t wst1 = wst + (int64_t)a.g.tw;
+    if (w >= wst1) {
+      h.t1 = tile_base + t + 1;
+      h.off1 = (uint32_t)((int64_t)J - 32 * wst1);
+    }
+  }
+  return h;
+}
+
+__device__ __forceinline__ void bucket_reserve(const BucketArgs &a, BucketHit &h) {
+  h.i0 = atomicAdd(&a.bucket_count[h.t0], 1u);
+  h.i1 = h.t1 != 0xFFFFFFFFu ? atomicAdd(&a.bucket_count[h.t1], 1u) : 0u;
+}
+
+__device__ __forceinline__ void bucket_store(const BucketArgs &a, const BucketHit &h) {
+  if (h.i0 < a.g.bucket_cap) a.bucket_data[(size_t)h.t0 * a.g.bucket_cap + h.i0] = h.off0;
+  else atomicOr(&a.hdr->status, kStBucketOverflow);
+  if (h.t1 != 0xFFFFFFFFu) {
+    if (h.i1 < a.g.bucket_cap) a.bucket_data[(size_t)h.t1 * a.g.bucket_cap + h.i1] = h.off1;
+    else atomicOr(&a.hdr->status, kStBucketOverflow);
+  }
+}
+
+// The struck bits J[0 .. n-1] (n <= kHitBatch) of one range: all slots are
+// reserved before any entry is written.
+__device__ __forceinline__ void bucket_emit(const BucketArgs &a, const uint64_t (&J)[kHitBatch], uint32_t n,
+                                            int64_t w0, uint32_t tile_base, uint32_t n_tiles) {
+  BucketHit h[kHitBatch];
+#pragma unroll
+  for (uint32_t u = 0; u < kHitBatch; ++u)
+    if (u < n) h[u] = bucket_hit(a, J[u], w0, tile_base, n_tiles);
+#pragma unroll
+  for (uint32_t u = 0; u < kHitBatch; ++u)
+    if (u < n) bucket_reserve(a, h[u]);
+#pragma unroll
+  for (uint32_t u = 0; u < kHitBatch; ++u)
+    if (u < n) bucket_store(a, h[u]);
+}
+
+// ---- Barrett items ----------------------------------------------------------
+// Primes of prime block pb (one per thread) against the ranges of request
+// chunk rc.
+__device__ void fill_barrett_item(const BucketArgs &a, FillReq *s_req, uint32_t pb, uint32_t rc, uint32_t n_reqs,
+                                  uint32_t prime_end) {
+  const uint32_t r0 = rc * kFillReqChunk;
+  const uint32_t nr = min(kFillReqChunk, n_reqs - r0);
+  __syncthreads();  // s_req holds the previous item's ranges
+  for (uint32_t r = threadIdx.x; r < nr; r += blockDim.x) {
+    const ReqDesc &R = a.reqs[r0 + r];
+    FillReq f;
+    const int64_t ws = R.w0 - (int64_t)a.g.mw;
+    f.A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
+    f.E = R.jhi;
+    f.w0 = R.w0;
+    f.tile_base = R.tile_base;
+    f.n_tiles = R.n_tiles;
+    f.n_primes = R.n_primes;
+    f.pad = 0;
+    s_req[r] = f;
+  }
+  __syncthreads();
+  const uint32_t pi = a.g.i_large + pb * blockDim.x + threadIdx.x;
+  if (pi >= prime_end) return;
+  const uint64_t p = a.pt.p[pi];
+  const uint64_t q = p * p, mu = a.pt.mu[pi];
+  for (uint32_t r = 0; r < nr; ++r) {
+    const FillReq f = s_req[r];
+    if (pi >= f.n_primes || f.n_tiles == 0 || f.E <= f.A) continue;
+    for (uint64_t J = f.A + first_strike(f.A, q, mu); J < f.E; J += kHitBatch * q) {
+      uint64_t Jv[kHitBatch];
+      uint32_t n = 0;
+#pragma unroll
+      for (uint32_t u = 0; u < kHitBatch; ++u) {
+        Jv[u] = J + u * q;
+        if (Jv[u] < f.E) n = u + 1;
+      }
+      bucket_emit(a, Jv, n, f.w0, f.tile_base, f.n_tiles);
+    }
+  }
+}
+
+// ---- multiplier items -------------------------------------------------------
+
+// floor(sqrt(x)) by Newton's iteration from above (integer only).
+__device__ __forceinline__ uint64_t isqrt_floor(uint64_t x) {
+  if (x < 2) return x;
+  const int bits = 64 - __clzll((long long)x);
+  uint64_t r = 1ull << ((bits + 1) >> 1);  // >= sqrt(x)
+  for (;;) {
+    const uint64_t y = (r + x / r) >> 1;
+    if (y >= r) return r;
+    r = y;
+  }
+}
+
+// Bitmap bits [b0, b1] ((p-1)/2) of the odd p >= ph, p <= p_top, with an odd
+// multiple j p^2 in [mlo, mhi]; false if there are none.  An odd multiple
+// m = j p^2 lies in [mlo, mhi] exactly when
+// ceil(sqrt(ceil(mlo/j))) <= p <= floor(sqrt(floor(mhi/j))).
+__device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t j, uint64_t ph, uint64_t p_top,
+                                           uint64_t *b0, uint64_t *b1) {
+  const uint64_t lq = (mlo + j - 1) / j, hq = mhi / j;
+  uint64_t plo = isqrt_floor(lq - 1) + 1, phi = isqrt_floor(hq);
+  if (plo < ph) plo = ph;
+  if (phi > p_top) phi = p_top;
+  if (plo > phi) return false;
+  *b0 = plo >> 1;
+  *b1 = (phi - 1) >> 1;
+  return *b0 <= *b1;
+}
+
+// The primes of bitmap word wd (bits m) with multiplier j: their struck bits
+// (j p^2 - 1) / 2, one at a time (batching them here costs more registers
+// than the whole kernel otherwise needs).
+__device__ __forceinline__ void emit_word(const BucketArgs &a, const ReqDesc &R, uint32_t m, uint64_t wd,
+                                          uint64_t j) {
+  while (m) {
+    const uint32_t bb = __ffs(m) - 1;
+    m &= m - 1;
+    const uint64_t p = 2 * (32 * wd + bb) + 1;
+    const uint64_t Jv[kHitBatch] = {(p * p * j - 1) >> 1, 0, 0, 0};
+    bucket_emit(a, Jv, 1, R.w0, R.tile_base, R.n_tiles);
+  }
+}
+
+// Bitmap word w of the interval [b0, b1], masked to it.
+__device__ __forceinline__ uint32_t interval_word(const BucketArgs &a, uint64_t w, uint64_t b0, uint64_t b1) {
+  uint32_t mm = a.pt.bits[w];
+  if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
+  if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
+  return mm;
+}
+
+// Slice s of nsl of range r's odd multipliers j (j p^2 in the range, p >= p_hyb).
+// The smallest multipliers have the longest p intervals (and the most hits).
+// A long range (>= 2^30 odd numbers) spreads their bitmap words over the
+// threads of all slices, j by j, with the intervals computed once per item;
+// a shorter one gives each small j to one warp, lanes striding over words.
+// Larger j take one thread each.
+__device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[2], uint32_t s, uint32_t nsl, uint32_t r) {
+  const Geometry &g = a.g;
+  const ReqDesc &R = a.reqs[r];
+  if (R.n_tiles == 0 || R.n_primes <= g.i_hyb) return;  // uniform over the block
+  const int64_t ws = R.w0 - (int64_t)g.mw;
+  const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws), E = R.jhi;
+  if (E <= A) return;
+  const uint64_t ph = g.p_hyb, ph2 = ph * ph;
+  const uint64_t mlo = 2 * A + 1, mhi = 2 * E - 1;
+  const uint64_t jmax = mhi / ph2;
+  const uint64_t p_top = a.pt.p[R.n_primes - 1];  // primes with p^2 < hi
+  const uint64_t w_end = a.pt.bits_words;
+  if (E - A >= (1ull << 30)) {
+    __syncthreads();  // s_iv holds the previous item's intervals
+    if (threadIdx.x < kWarpJ) {
+      const uint64_t j = 2 * threadIdx.x + 1;
+      uint64_t b0 = 1, b1 = 0;
+      if (j > jmax || !p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) b0 = 1, b1 = 0;
+      s_iv[threadIdx.x][0] = b0;
+      s_iv[threadIdx.x][1] = b1;
+    }
+    __syncthreads();
+    const uint64_t gx = (uint64_t)s * blockDim.x + threadIdx.x, nx = (uint64_t)nsl * blockDim.x;
+    for (uint32_t t = 0; t < kWarpJ; ++t) {
+      const uint64_t b0 = s_iv[t][0], b1 = s_iv[t][1];
+      if (b1 < b0) continue;
+      const uint64_t w_last = min(b1 >> 5, w_end - 1);
+      for (uint64_t w = (b0 >> 5) + gx; w <= w_last; w += nx) emit_word(a, R, interval_word(a, w, b0, b1), w, 2 * t + 1);
+    }
+  } else {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t wpb = blockDim.x >> 5;
+    for (uint64_t t = (uint64_t)s * wpb + (threadIdx.x >> 5); t < kWarpJ && 2 * t + 1 <= jmax; t += (uint64_t)nsl * wpb) {
+      const uint64_t j = 2 * t + 1;
+      uint64_t b0, b1;
+      if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+      const uint64_t w_last = min(b1 >> 5, w_end - 1);
+      for (uint64_t w = (b0 >> 5) + lane; w <= w_last; w += 32) emit_word(a, R, interval_word(a, w, b0, b1), w, j);
+    }
+  }
+  for (uint64_t t = kWarpJ + (uint64_t)s * blockDim.x + threadIdx.x; 2 * t + 1 <= jmax;
+       t += (uint64_t)nsl * blockDim.x) {
+    const uint64_t j = 2 * t + 1;
+    uint64_t b0, b1;
+    if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+    const uint64_t w_last = min(b1 >> 5, w_end - 1);
+    for (uint64_t wd = b0 >> 5; wd <= w_last; wd += 4) {  // four words in flight
+      uint32_t m[4];
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) m[u] = wd + u <= w_last ? interval_word(a, wd + u, b0, b1) : 0u;
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) emit_word(a, R, m[u], wd + u, j);
+    }
+  }
+}
+
+// The item space: px prime blocks x py request chunks of Barrett items, then
+// jx slices x jy requests of multiplier items (host-chosen upper bounds).
+// Each is trimmed to what the launch's header asks for, so that a captured
+// launch sized for its buffers wastes no block on absent work.
+struct FillItems {
+  uint32_t px, py, jx, jy;
+};
+
+__global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_kernel(BucketArgs a, FillItems fi) {
+  __shared__ FillReq s_req[kFillReqChunk];
+  __shared__ uint64_t s_iv[kWarpJ][2];
+  const Geometry &g = a.g;
+  const uint32_t n_reqs = a.hdr->n_reqs;
+  const uint32_t max_primes = a.hdr->max_primes;
+  // Barrett items actually present
+  const uint32_t prime_end = min(max_primes, g.i_hyb);
+  const uint32_t n_pblocks = prime_end > g.i_large ? (prime_end - g.i_large + blockDim.x - 1) / blockDim.x : 0u;
+  const uint32_t n_chunks = (n_reqs + kFillReqChunk - 1) / kFillReqChunk;
+  const uint32_t px = min(fi.px, n_pblocks), py = min(fi.py, n_chunks);
+  const uint32_t n_bar = px * py;  // <= 4096 * 64
+  // multiplier items actually present
+  const uint32_t jx = (max_primes > g.i_hyb && g.p_hyb != 0xFFFFFFFFu) ? fi.jx : 0u;
+  const uint32_t jy = min(fi.jy, n_reqs);
+  const uint32_t n_mult = jx * jy;  // <= 64 * 1024
+  // Blocks take items round robin.  The multiplier items come first, slice
+  // by slice: the low slices hold the small multipliers, the costliest
+  // items, and consecutive items land on different blocks.
+  for (uint32_t it = blockIdx.x; it < n_mult + n_bar; it += gridDim.x) {
+    if (it < n_mult) {
+      // item (s, ry) covers slice s of the ranges ry + jy k
+      for (uint32_t r = it % jy; r < n_reqs; r += jy) fill_mult_item(a, s_iv, it / jy, jx, r);
+    } else {
+      const uint32_t m = it - n_mult;
+      // item (pbx, rcy) covers prime blocks pbx + px i and chunks rcy + py k
+      for (uint32_t rc = m / px; rc < n_chunks; rc += py)
+        for (uint32_t pb = m % px; pb < n_pblocks; pb += px) fill_barrett_item(a, s_req, pb, rc, n_reqs, prime_end);
+    }
+  }
+}
+
+cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs, uint64_t j_max,
+                               uint32_t max_blocks, cudaStream_t st) {
+  if (n_large_max == 0 || n_reqs == 0) return cudaSuccess;
+  FillItems fi;
+  fi.px = (uint32_t)std::min<uint64_t>((n_large_max + kFillThreads - 1) / kFillThreads, 4096);
+  fi.py = std::min<uint32_t>((n_reqs + kFillReqChunk - 1) / kFillReqChunk, 64);
+  const bool mult = a.g.p_hyb != 0xFFFFFFFFu && j_max != 0;
+  fi.jx = mult ? (uint32_t)std::min<uint64_t>((j_max / 2 + kFillThreads) / kFillThreads, 64) : 0u;
+  fi.jy = mult ? std::min<uint32_t>(n_reqs, 1024) : 0u;
+  const uint64_t items = (uint64_t)fi.px * fi.py + (uint64_t)fi.jx * fi.jy;
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(items, max_blocks ? max_blocks : 1));
+  bucket_fill_kernel<<<grid, kFillThreads, 0, st>>>(a, fi);
+  return cudaGetLastError();
+}
+
+}  // namespace sv

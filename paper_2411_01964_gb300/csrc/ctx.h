@@ -135,7 +135,7 @@ struct sv_ctx {
   bool pending_graph = false;
   std::vector<sv::RangeSpec> pending_specs;
   // per-kernel timing with events on the launching stream (sv_kernel_timing)
-  bool kprof = false;
+  uint32_t kprof = 0;  // kernel ids timed with events (bit i: id i)
   struct KEv {
     int id;
     cudaEvent_t a, b;

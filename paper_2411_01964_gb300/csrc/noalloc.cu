@@ -238,7 +238,8 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
       b.bucket_data = d_bdata;
       const uint64_t ph2 = g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb;
       const uint64_t jmax = ph2 ? (2 * d.jhi - 1) / ph2 : 0;
-      if (launch_bucket_fill(b, d.n_primes - g.i_large, 1, jmax, st) != cudaSuccess) return SV_ECUDA;
+      if (launch_bucket_fill(b, d.n_primes - g.i_large, 1, jmax, (uint32_t)c->num_sms * kFillBlocksPerSm, st) != cudaSuccess)
+        return SV_ECUDA;
       c->launches++;
     }
     TileArgs t{};

@@ -179,10 +179,11 @@ struct CompactArgs {
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, cudaStream_t st);
 cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st);
-// j_max: the largest number of odd multipliers any range of the launch needs
-// for the primes >= p_hyb (sizes the enumeration grid).
+// n_large_max, n_reqs: upper bounds of the launch's bucket primes and ranges;
+// j_max: the largest odd multiplier any range needs for the primes >= p_hyb.
+// They size the work items; at most max_blocks blocks take them in turn.
 cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs, uint64_t j_max,
-                               cudaStream_t st);
+                               uint32_t max_blocks, cudaStream_t st);
 // mode 0: lean scan (lists from k >= 6, no per-n output); 1: general scan;
 // 2: general scan writing the per-n output.
 cudaError_t launch_tiles(const TileArgs &a, uint32_t threads, uint32_t grid, size_t smem, int mode,
@@ -199,5 +200,6 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
 constexpr int kMaxDensePrimes = 128;  // must match the tile kernel's shared arrays (four warps)
 constexpr int kDenseMinHits = 4;      // primes with at least this many strikes per window are "dense"
 constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)
+constexpr uint32_t kFillBlocksPerSm = 4;  // resident bucket-fill blocks per SM (the launch bounds)
 
 }  // namespace sv

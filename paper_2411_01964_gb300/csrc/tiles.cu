@@ -18,7 +18,7 @@
 //              ones take one thread per prime.  The offsets of both carry
 //              from a window to the next one of the same range.  Larger
 //              primes arrive as precomputed bit offsets in the tile's bucket
-//              (bucket_fill_kernel, bucket_fill_j_kernel);
+//              (bucket_fill_kernel, buckets.cu);
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
 //              flags of n - 2^k are word i shifted by 2^(k-1) bits: a funnel
 //              shift of (w[i-1], w[i]) for k <= 5, the word w[i - 2^(k-6)] for
@@ -35,27 +35,10 @@
 // The bitmap never leaves shared memory.
 #include <cuda_runtime.h>
 
+#include "strike.h"
 #include "sv_internal.h"
 
 namespace sv {
-
-// x mod q for q >= 2 with mu = floor((2^64-1)/q): Barrett (1986) reduction.
-// The estimate t = floor(x*mu / 2^64) is at most 2 below floor(x/q).
-__device__ __forceinline__ uint64_t mod_barrett(uint64_t x, uint64_t q, uint64_t mu) {
-  const uint64_t t = __umul64hi(x, mu);
-  uint64_t r = x - t * q;
-  if (r >= q) r -= q;
-  if (r >= q) r -= q;
-  return r;
-}
-
-// Odd multiples of q = p^2 are the integers q(2i+1), i.e. the bits
-// J = q*i + (q-1)/2.  Offset (from bit A) of the first such bit >= A.
-__device__ __forceinline__ uint64_t first_strike(uint64_t A, uint64_t q, uint64_t mu) {
-  const uint64_t r = mod_barrett(A, q, mu);
-  const uint64_t c = (q - 1) >> 1;
-  return (c >= r) ? (c - r) : (c + q - r);
-}
 
 // The stamped primes (the smallest ones, applied by the word's owner as a
 // computed pattern instead of shared-memory atomics): q = p^2 and the 32-bit
@@ -201,299 +184,6 @@ cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
   if (grid < 1) grid = 1;
   if (grid > 1024) grid = 1024;
   init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// bucket fill: for every large prime and every range, the struck bits of the
-// range's windows, appended to the bucket of each tile whose window holds them
-// (the tile's core, and the next tile's look-back margin).
-// ---------------------------------------------------------------------------
-constexpr uint32_t kFillReqChunk = 64;
-
-struct FillReq {
-  uint64_t A, E;       // struck bits wanted: [A, E)
-  int64_t w0;
-  uint32_t tile_base, n_tiles, n_primes, pad;
-};
-
-__device__ __forceinline__ void bucket_push(const BucketArgs &a, uint32_t gtile, uint32_t off) {
-  const uint32_t idx = atomicAdd(&a.bucket_count[gtile], 1u);
-  if (idx < a.g.bucket_cap)
-    a.bucket_data[(size_t)gtile * a.g.bucket_cap + idx] = off;
-  else
-    atomicOr(&a.hdr->status, kStBucketOverflow);
-}
-
-// A struck bit J of a range: into the bucket of the tile whose core holds it,
-// and into the next tile's bucket if J also lies in that tile's look-back.
-__device__ __forceinline__ void bucket_emit(const BucketArgs &a, uint64_t J, int64_t w0, uint32_t tile_base,
-                                            uint32_t n_tiles) {
-  const int64_t w = (int64_t)(J >> 5);
-  uint32_t t = 0;
-  if (w >= w0) t = (uint32_t)((uint64_t)(w - w0) >> a.g.tw_log2);
-  if (t >= n_tiles) t = n_tiles - 1;  // cannot happen: J < E
-  const int64_t wst = w0 + (int64_t)t * a.g.tw - (int64_t)a.g.mw;
-  bucket_push(a, tile_base + t, (uint32_t)((int64_t)J - 32 * wst));
-  if (t + 1 < n_tiles) {
-    const int64_t wst1 = wst + (int64_t)a.g.tw;
-    if (w >= wst1) bucket_push(a, tile_base + t + 1, (uint32_t)((int64_t)J - 32 * wst1));
-  }
-}
-
-// One struck bit's bucket entries, computed before their slots are reserved:
-// the tile whose core holds it and, if it also lies in the next tile's
-// look-back, that tile (t1 = 0xFFFFFFFF: none).
-struct BucketHit {
-  uint32_t t0, off0, t1, off1, i0, i1;
-};
-__device__ __forceinline__ BucketHit bucket_hit(const BucketArgs &a, uint64_t J, int64_t w0, uint32_t tile_base,
-                                                uint32_t n_tiles) {
-  BucketHit h;
-  const int64_t w = (int64_t)(J >> 5);
-  uint32_t t = 0;
-  if (w >= w0) t = (uint32_t)((uint64_t)(w - w0) >> a.g.tw_log2);
-  if (t >= n_tiles) t = n_tiles - 1;  // cannot happen: J < E
-  const int64_t wst = w0 + (int64_t)t * a.g.tw - (int64_t)a.g.mw;
-  h.t0 = tile_base + t;
-  h.off0 = (uint32_t)((int64_t)J - 32 * wst);
-  h.t1 = 0xFFFFFFFFu;
-  h.off1 = 0;
-  if (t + 1 < n_tiles) {
-    const int64_t wst1 = wst + (int64_t)a.g.tw;
-    if (w >= wst1) {
-      h.t1 = tile_base + t + 1;
-      h.off1 = (uint32_t)((int64_t)J - 32 * wst1);
-    }
-  }
-  return h;
-}
-__device__ __forceinline__ void bucket_reserve(const BucketArgs &a, BucketHit &h) {
-  h.i0 = atomicAdd(&a.bucket_count[h.t0], 1u);
-  h.i1 = h.t1 != 0xFFFFFFFFu ? atomicAdd(&a.bucket_count[h.t1], 1u) : 0u;
-}
-__device__ __forceinline__ void bucket_store(const BucketArgs &a, const BucketHit &h) {
-  if (h.i0 < a.g.bucket_cap) a.bucket_data[(size_t)h.t0 * a.g.bucket_cap + h.i0] = h.off0;
-  else atomicOr(&a.hdr->status, kStBucketOverflow);
-  if (h.t1 != 0xFFFFFFFFu) {
-    if (h.i1 < a.g.bucket_cap) a.bucket_data[(size_t)h.t1 * a.g.bucket_cap + h.i1] = h.off1;
-    else atomicOr(&a.hdr->status, kStBucketOverflow);
-  }
-}
-
-// Primes i_large <= i < i_hyb: one thread per prime, one Barrett reduction
-// per range for its first struck bit, then every further hit.
-__global__ void __launch_bounds__(256) bucket_fill_kernel(BucketArgs a) {
-  __shared__ FillReq s_req[kFillReqChunk];
-  const uint32_t n_reqs = a.hdr->n_reqs;
-  const uint32_t max_primes = min(a.hdr->max_primes, a.g.i_hyb);
-  const Geometry g = a.g;
-  if (max_primes <= g.i_large) return;
-  const uint32_t n_large = max_primes - g.i_large;
-  const uint32_t n_pblocks = (n_large + blockDim.x - 1) / blockDim.x;
-  const uint32_t mw = g.mw;
-
-  for (uint32_t pb = blockIdx.x; pb < n_pblocks; pb += gridDim.x) {
-    const uint32_t pi = g.i_large + pb * blockDim.x + threadIdx.x;
-    const bool act = pi < max_primes;
-    uint64_t q = 1, mu = 0;
-    if (act) {
-      const uint64_t p = a.pt.p[pi];
-      q = p * p;
-      mu = a.pt.mu[pi];
-    }
-    for (uint32_t rc = blockIdx.y * kFillReqChunk; rc < n_reqs; rc += gridDim.y * kFillReqChunk) {
-      const uint32_t nr = min(kFillReqChunk, n_reqs - rc);
-      __syncthreads();
-      for (uint32_t r = threadIdx.x; r < nr; r += blockDim.x) {
-        const ReqDesc &R = a.reqs[rc + r];
-        FillReq f;
-        const int64_t ws = R.w0 - (int64_t)mw;
-        f.A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
-        f.E = R.jhi;
-        f.w0 = R.w0;
-        f.tile_base = R.tile_base;
-        f.n_tiles = R.n_tiles;
-        f.n_primes = R.n_primes;
-        s_req[r] = f;
-      }
-      __syncthreads();
-      if (!act) continue;
-      for (uint32_t r = 0; r < nr; ++r) {
-        const FillReq f = s_req[r];
-        if (pi >= f.n_primes || f.n_tiles == 0 || f.E <= f.A) continue;
-        uint64_t J = f.A + first_strike(f.A, q, mu);
-        // four hits at a time: their slot reservations go out together, so
-        // the atomics' round trips overlap instead of queueing one by one
-        for (; J + 3 * q < f.E; J += 4 * q) {
-          BucketHit h0 = bucket_hit(a, J, f.w0, f.tile_base, f.n_tiles);
-          BucketHit h1 = bucket_hit(a, J + q, f.w0, f.tile_base, f.n_tiles);
-          BucketHit h2 = bucket_hit(a, J + 2 * q, f.w0, f.tile_base, f.n_tiles);
-          BucketHit h3 = bucket_hit(a, J + 3 * q, f.w0, f.tile_base, f.n_tiles);
-          bucket_reserve(a, h0);
-          bucket_reserve(a, h1);
-          bucket_reserve(a, h2);
-          bucket_reserve(a, h3);
-          bucket_store(a, h0);
-          bucket_store(a, h1);
-          bucket_store(a, h2);
-          bucket_store(a, h3);
-        }
-        for (; J < f.E; J += q) bucket_emit(a, J, f.w0, f.tile_base, f.n_tiles);
-      }
-    }
-  }
-}
-
-// floor(sqrt(x)) by Newton's iteration from above (integer only).
-__device__ __forceinline__ uint64_t isqrt_floor(uint64_t x) {
-  if (x < 2) return x;
-  const int bits = 64 - __clzll((long long)x);
-  uint64_t r = 1ull << ((bits + 1) >> 1);  // >= sqrt(x)
-  for (;;) {
-    const uint64_t y = (r + x / r) >> 1;
-    if (y >= r) return r;
-    r = y;
-  }
-}
-
-// Primes p >= p_hyb (index >= i_hyb): instead of reducing the window start
-// modulo every p^2, enumerate the odd multipliers j.  An odd multiple m =
-// j p^2 lies in the window's odd integers [2A+1, 2E-1] exactly when
-// ceil(sqrt(ceil((2A+1)/j))) <= p <= floor(sqrt(floor((2E-1)/j))); the primes
-// of that interval are read from the prime bitmap, 32 candidates per word
-// (four words in flight).  One thread per (range, j); j <= (2E-1) / p_hyb^2.
-__device__ __forceinline__ void emit_word(const BucketArgs &a, const ReqDesc &R, uint32_t m, uint64_t wd, uint64_t j) {
-  while (m) {
-    const uint32_t bb = __ffs(m) - 1;
-    m &= m - 1;
-    const uint64_t p = 2 * (32 * wd + bb) + 1;
-    bucket_emit(a, (p * p * j - 1) >> 1, R.w0, R.tile_base, R.n_tiles);
-  }
-}
-
-constexpr uint64_t kWarpJ = 32;  // odd j < 2 kWarpJ are handled cooperatively (warp or grid)
-
-// Bitmap bits [b0, b1] ((p-1)/2) of the odd p >= ph, p <= p_top, with an odd
-// multiple j p^2 in [mlo, mhi]; false if there are none.
-__device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t j, uint64_t ph, uint64_t p_top,
-                                           uint64_t *b0, uint64_t *b1) {
-  const uint64_t lq = (mlo + j - 1) / j, hq = mhi / j;
-  uint64_t plo = isqrt_floor(lq - 1) + 1, phi = isqrt_floor(hq);
-  if (plo < ph) plo = ph;
-  if (phi > p_top) phi = p_top;
-  if (plo > phi) return false;
-  *b0 = plo >> 1;
-  *b1 = (phi - 1) >> 1;
-  return *b0 <= *b1;
-}
-
-__global__ void __launch_bounds__(256) bucket_fill_j_kernel(BucketArgs a) {
-  __shared__ uint64_t s_iv[kWarpJ][2];  // bitmap bits [b0, b1] of the small multipliers' p intervals
-  const uint32_t n_reqs = a.hdr->n_reqs;
-  const Geometry g = a.g;
-  if (a.hdr->max_primes <= g.i_hyb) return;
-  const uint64_t ph = g.p_hyb, ph2 = ph * ph;
-  const uint32_t mw = g.mw;
-  for (uint32_t r = blockIdx.y; r < n_reqs; r += gridDim.y) {
-    const ReqDesc &R = a.reqs[r];
-    if (R.n_tiles == 0 || R.n_primes <= g.i_hyb) continue;
-    const int64_t ws = R.w0 - (int64_t)mw;
-    const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws), E = R.jhi;
-    if (E <= A) continue;
-    const uint64_t mlo = 2 * A + 1, mhi = 2 * E - 1;
-    const uint64_t jmax = mhi / ph2;
-    const uint64_t p_top = a.pt.p[R.n_primes - 1];  // primes with p^2 < hi
-    // the smallest multipliers have the longest p intervals (and the most
-    // hits).  A long range (>= 2^30 odd numbers) spreads their bitmap words
-    // over all the x-threads of the grid, j by j, with the intervals computed
-    // once per block; a shorter one gives each small j to one warp, lanes
-    // striding over words.
-    const bool spread = E - A >= (1ull << 30);
-    if (spread) {
-      __syncthreads();  // s_iv is reused for every range
-      if (threadIdx.x < kWarpJ) {
-        const uint64_t j = 2 * threadIdx.x + 1;
-        uint64_t b0 = 1, b1 = 0;
-        if (j > jmax || !p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) b0 = 1, b1 = 0;
-        s_iv[threadIdx.x][0] = b0;
-        s_iv[threadIdx.x][1] = b1;
-      }
-      __syncthreads();
-      const uint64_t gx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nx = (uint64_t)gridDim.x * blockDim.x;
-      for (uint32_t t = 0; t < kWarpJ; ++t) {
-        const uint64_t b0 = s_iv[t][0], b1 = s_iv[t][1];
-        if (b1 < b0) continue;
-        const uint64_t j = 2 * t + 1;
-        uint64_t w_last = b1 >> 5;
-        if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
-        for (uint64_t w = (b0 >> 5) + gx; w <= w_last; w += nx) {
-          uint32_t mm = a.pt.bits[w];
-          if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
-          if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
-          emit_word(a, R, mm, w, j);
-        }
-      }
-    } else {
-      const uint32_t lane = threadIdx.x & 31u;
-      const uint64_t wpb = blockDim.x >> 5;
-      for (uint64_t t = (uint64_t)blockIdx.x * wpb + (threadIdx.x >> 5); t < kWarpJ && 2 * t + 1 <= jmax;
-           t += (uint64_t)gridDim.x * wpb) {
-        const uint64_t j = 2 * t + 1;
-        uint64_t b0, b1;
-        if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
-        uint64_t w_last = b1 >> 5;
-        if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
-        for (uint64_t w = (b0 >> 5) + lane; w <= w_last; w += 32) {
-          uint32_t mm = a.pt.bits[w];
-          if (w == (b0 >> 5)) mm &= 0xFFFFFFFFu << (b0 & 31);
-          if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
-          emit_word(a, R, mm, w, j);
-        }
-      }
-    }
-    // the rest: one thread per j
-    for (uint64_t t = kWarpJ + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * t + 1 <= jmax;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-      const uint64_t j = 2 * t + 1;
-      uint64_t b0, b1;
-      if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
-      const uint64_t w_first = b0 >> 5;
-      uint64_t w_last = b1 >> 5;
-      if (w_last >= a.pt.bits_words) w_last = a.pt.bits_words - 1;
-      for (uint64_t wd = w_first; wd <= w_last; wd += 4) {
-        uint32_t m[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) m[u] = (wd + u <= w_last) ? a.pt.bits[wd + u] : 0u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint64_t w = wd + u;
-          if (w > w_last) break;
-          uint32_t mm = m[u];
-          if (w == w_first) mm &= 0xFFFFFFFFu << (b0 & 31);
-          if (w == (b1 >> 5) && (b1 & 31) != 31) mm &= (2u << (b1 & 31)) - 1u;
-          emit_word(a, R, mm, w, j);
-        }
-      }
-    }
-  }
-}
-
-cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32_t n_reqs, uint64_t j_max,
-                               cudaStream_t st) {
-  if (n_large_max == 0 || n_reqs == 0) return cudaSuccess;
-  const uint32_t threads = 256;
-  uint32_t gx = (n_large_max + threads - 1) / threads;
-  uint32_t gy = (n_reqs + kFillReqChunk - 1) / kFillReqChunk;
-  if (gx > 4096) gx = 4096;
-  if (gy > 64) gy = 64;
-  bucket_fill_kernel<<<dim3(gx, gy), threads, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || a.g.p_hyb == 0xFFFFFFFFu || j_max == 0) return e;
-  uint64_t jx = (j_max / 2 + threads) / threads;  // one thread per odd j
-  if (jx > 64) jx = 64;
-  const uint32_t jy = n_reqs > 1024 ? 1024 : n_reqs;
-  bucket_fill_j_kernel<<<dim3((uint32_t)jx, jy), threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1134,126 +824,6 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       __syncwarp();
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// The ordered list (mode 0).  The launch's tiles are cut into blocks of 1024,
-// one thread per tile; a tile's place in its range's list is the number of
-// entries its range staged in the tiles before it: the block's inclusive
-// scan (segmented at range starts) plus, for a range that began in an
-// earlier block, the sum of its staged counts there.  Each tile's few
-// entries arrive unordered and are ranked among themselves, so the list
-// comes out ascending.  Entries past the range's list capacity are counted,
-// not stored: the smallest ones are kept.  The thread of a range's last tile
-// writes the range's total.
-// ---------------------------------------------------------------------------
-constexpr uint32_t kCompactBlock = 1024;
-constexpr uint32_t kRankRegs = 8;  // staged entries of a tile ranked in registers (more: from memory)
-
-__device__ __forceinline__ uint32_t range_of_tile(const ReqDesc *reqs, uint32_t n_reqs, uint32_t t) {
-  uint32_t lo = 0, hi = n_reqs;
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (reqs[mid].tile_base <= t) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-__global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactArgs a) {
-  __shared__ uint32_t incl_s[kCompactBlock];
-  __shared__ uint32_t wsum[32];
-  __shared__ uint32_t carry_s;
-  const uint32_t n_reqs = a.hdr->n_reqs, total = a.hdr->total_tiles;
-  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t nblk = (total + kCompactBlock - 1) / kCompactBlock;
-  for (uint32_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const uint32_t b0 = blk * kCompactBlock;
-    const uint32_t t = b0 + tid;
-    const bool act = t < total;
-    const uint32_t r = act ? range_of_tile(a.reqs, n_reqs, t) : 0u;
-    const ReqDesc *R = act ? &a.reqs[r] : nullptr;
-    const bool listed = act && !R->sieve_only && t - R->tile_base < R->n_tiles;
-    const uint32_t cnt = listed ? min(a.stage_cnt[t], a.stage_cap) : 0u;
-    // carry-in: the staged entries of the block's first range before the block
-    if (tid == 0) carry_s = 0;
-    __syncthreads();
-    {
-      const uint32_t r0 = range_of_tile(a.reqs, n_reqs, b0);
-      const uint32_t tb0 = a.reqs[r0].tile_base;
-      uint32_t part = 0;
-      if (!a.reqs[r0].sieve_only)
-        for (uint32_t u = tb0 + tid; u < b0; u += kCompactBlock) part += min(a.stage_cnt[u], a.stage_cap);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
-      if (lane == 0 && part) atomicAdd(&carry_s, part);
-    }
-    // inclusive block scan of the counts
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-      if (lane >= (uint32_t)o) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const uint32_t w = wsum[lane];
-      uint32_t wi = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-        if (lane >= (uint32_t)o) wi += y;
-      }
-      wsum[lane] = wi - w;
-    }
-    __syncthreads();
-    incl += wsum[warp];
-    incl_s[tid] = incl;
-    __syncthreads();
-    if (listed) {
-      // entries of this range in the block's tiles before t, plus the carry-in
-      const uint32_t s0 = R->tile_base > b0 ? R->tile_base - b0 : 0u;
-      uint64_t pos = (uint64_t)(incl - cnt) - (s0 ? incl_s[s0 - 1] : 0u);
-      if (R->tile_base < b0) pos += carry_s;
-      const uint64_t *sn = a.stage_n + (size_t)t * kStageCap;
-      const uint8_t *sk = a.stage_k + (size_t)t * kStageCap;
-      if (cnt <= kRankRegs) {
-        // the usual case: a few entries, ranked in registers
-        uint64_t v[kRankRegs];
-#pragma unroll
-        for (uint32_t e = 0; e < kRankRegs; ++e) v[e] = e < cnt ? sn[e] : ~0ull;
-#pragma unroll
-        for (uint32_t e = 0; e < kRankRegs; ++e) {
-          if (e >= cnt) break;
-          uint32_t rank = 0;
-#pragma unroll
-          for (uint32_t f = 0; f < kRankRegs; ++f) rank += v[f] < v[e] ? 1u : 0u;
-          if (pos + rank < R->list_cap) {
-            a.list_n[R->list_off + pos + rank] = v[e];
-            a.list_k[R->list_off + pos + rank] = sk[e];
-          }
-        }
-      } else {
-        for (uint32_t e = 0; e < cnt; ++e) {
-          const uint64_t n = sn[e];
-          uint32_t rank = 0;
-          for (uint32_t f = 0; f < cnt; ++f) rank += sn[f] < n ? 1u : 0u;
-          if (pos + rank < R->list_cap) {
-            a.list_n[R->list_off + pos + rank] = n;
-            a.list_k[R->list_off + pos + rank] = sk[e];
-          }
-        }
-      }
-      if (t - R->tile_base == R->n_tiles - 1) a.slots[R->slot].list_count = pos + cnt;
-    }
-    __syncthreads();  // the shared arrays are reused by the next block
-  }
-}
-
-cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st) {
-  if (grid == 0) return cudaSuccess;
-  list_compact_kernel<<<grid, kCompactBlock, 0, st>>>(a);
-  return cudaGetLastError();
 }
 
 // The stamped-prime counts instantiated (sv_config.stamp_primes).

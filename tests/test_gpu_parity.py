@@ -211,6 +211,26 @@ def test_repeatable(gpu):
     assert a.hist == b.hist and np.array_equal(a.per_n_k, b.per_n_k)
 
 
+def test_kernel_timing_selects_kernels():
+    """Per-kernel event timing: a set of kernel ids times only those kernels."""
+    from paper_2411_01964_gb300 import binding as B
+    lo, hi = (1 << 40) + 1, (1 << 40) + (1 << 28)
+    with Verifier(max_hi=hi + 1) as v:
+        B.sv_kernel_timing(v.ctx, ["tile"])
+        v.launch_range(lo, hi)
+        v.fetch_range()
+        ms, n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["tile"])
+        assert n == 1 and ms > 0
+        for name in ("init", "bucket_fill", "stragglers", "list_compact"):
+            assert B.sv_kernel_time(v.ctx, B.KERNEL_IDS[name])[1] == 0, name
+        B.sv_kernel_timing(v.ctx, True)
+        v.launch_range(lo, hi)
+        v.fetch_range()
+        for name in ("init", "bucket_fill", "tile", "stragglers", "list_compact"):
+            assert B.sv_kernel_time(v.ctx, B.KERNEL_IDS[name])[1] == 1, name
+        B.sv_kernel_timing(v.ctx, False)
+
+
 def test_batch_graph_replay_and_recapture(orc):
     """Consecutive batches replay one captured graph; a batch that needs larger
     buffers re-captures it.  Every result equals the oracle's."""
