@@ -22,8 +22,11 @@
 //   3. scan:   word-parallel Algorithm 2.  For the 32 odd n of word i, the
 //              flags of n - 2^k are word i shifted by 2^(k-1) bits: a funnel
 //              shift of (w[i-1], w[i]) for k <= 5, the word w[i - 2^(k-6)] for
-//              6 <= k <= kwin.  unresolved &= ~flags; hist[k] += popc(newly).
-//              k = 1..4 run without votes (two words per lane); a word still
+//              6 <= k <= kwin.  unresolved &= ~flags, and hist[k] is the
+//              drop of popc(unresolved) at step k (the lean scan sums the
+//              counts after each step, hist[k] = U_(k-1) - U_k).
+//              k = 1..4 run without votes (two words per lane, a 64-bit
+//              load in the fast path); a word still
 //              unresolved after k = 5 is finished by its lane after the loop;
 //              n still unresolved after kwin go to the exact straggler test.
 //              Tiles that may hold a range's first occurrence of some k <= 5
@@ -403,27 +406,31 @@ __device__ __noinline__ void finish_word(const uint32_t *win, uint32_t i, uint32
   if (u) straggler_push(a, sh, u, J0, kwin + 1u);
 }
 
-// k = K for two words at once (independent chains for the scheduler).
+// Step k = K on two words at once (independent chains for the scheduler):
+// the n whose n - 2^K is squarefree leave the unresolved sets.
 template <int K>
-__device__ __forceinline__ uint32_t step2(uint32_t p0, uint32_t w0, uint32_t p1, uint32_t w1, uint32_t &u0,
-                                          uint32_t &u1) {
-  const uint32_t h0 = u0 & __funnelshift_l(p0, w0, 1u << (K - 1));
-  const uint32_t h1 = u1 & __funnelshift_l(p1, w1, 1u << (K - 1));
-  u0 ^= h0;
-  u1 ^= h1;
-  return (uint32_t)(__popc(h0) + __popc(h1));
+__device__ __forceinline__ void step2(uint32_t p0, uint32_t w0, uint32_t p1, uint32_t w1, uint32_t &u0,
+                                      uint32_t &u1) {
+  u0 &= ~__funnelshift_l(p0, w0, 1u << (K - 1));
+  u1 &= ~__funnelshift_l(p1, w1, 1u << (K - 1));
 }
 
 // The lean scan (no per-n output, lists from k >= 6): each lane takes two
-// words per iteration, k = 1 is not counted, and words still unresolved
-// after k = 5 are queued for finish_word after the loop.  Tiles that may
-// still hold a range's first occurrence of some k <= 5 use scan_word.
+// words per iteration.  The counts telescope: with U_k the number of n still
+// unresolved after step k, hist[k] = U_(k-1) - U_k.  U_1 .. U_3 are summed
+// per word; U_4 is the k = 5 hits plus the n left after k = 5, both counted
+// in the rare branch that runs k = 5 (hist[1] follows from the number of valid
+// n at the end of the tile).  Words still unresolved after k = 5 are queued
+// for finish_word after the loop.  Tiles that may still hold a range's first
+// occurrence of some k <= 5 use scan_word.
 __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileArgs &a, ScanShared &sh,
                                                int64_t wstart, uint32_t nwords, uint32_t ifl, uint32_t nfull) {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t mw = a.g.mw;
   uint32_t need = sh.need;
-  uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+  uint32_t c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;  // hits of the scan_word path
+  uint32_t U1 = 0, U2 = 0, U3 = 0;                  // telescoped words: unresolved after k = 1, 2, 3
+  uint32_t c5t = 0, x5 = 0;                         // telescoped words: k = 5 hits, unresolved after k = 5
   // a word still unresolved after k = 5 waits in its lane (one at most; an
   // earlier one is finished first) and is finished after the loop
   uint32_t pend_i = 0, pend_u = 0;
@@ -433,22 +440,41 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
     pend_i = (I);                                                                   \
     pend_u = (U);                                                                   \
   }
-  if (need == 0u && ifl <= mw && nfull >= nwords - ifl && ((nwords - mw) & 63u) == 0u) {
+#define SV_K5(I0, I1)                                                               \
+  if (__any_sync(0xFFFFFFFFu, u0 | u1)) {                                           \
+    const uint32_t r4 = __popc(u0) + __popc(u1);                                    \
+    step2<5>(p0, w0, p1, w1, u0, u1);                                               \
+    const uint32_t r5 = __popc(u0) + __popc(u1);                                    \
+    c5t += r4 - r5;                                                                 \
+    x5 += r5;                                                                       \
+    SV_DEFER(I0, u0)                                                                \
+    SV_DEFER(I1, u1)                                                                \
+  }
+  if (need == 0u && ifl <= mw && nfull >= nwords - ifl && (nwords - mw) % (64u * nwarps) == 0u) {
     // every core word is in range and fully valid, and no first occurrence
-    // is searched: no masks, no bounds checks
-    for (uint32_t ib = mw + warp * 64u; ib < nwords; ib += nwarps * 64u) {
-      const uint32_t i0 = ib + lane, i1 = i0 + 32u;
-      const uint32_t w0 = win[i0], p0 = win[i0 - 1], w1 = win[i1], p1 = win[i1 - 1];
+    // is searched: no masks, no bounds checks.  Each warp scans one
+    // contiguous span, 64 words per step: lane l loads words 2l and 2l + 1
+    // at once; the word below 2l is lane l-1's second word (lane 0: the
+    // previous step's last word).
+    const uint32_t span = (nwords - mw) / nwarps;
+    const uint32_t ie = mw + (warp + 1u) * span;
+    uint32_t last = win[mw + warp * span - 1u];  // the same word for every lane
+    for (uint32_t ib = mw + warp * span; ib < ie; ib += 64u) {
+      const uint32_t i0 = ib + 2u * lane, i1 = i0 + 1u;
+      const uint2 ww = *reinterpret_cast<const uint2 *>(win + i0);
+      const uint32_t w0 = ww.x, w1 = ww.y, p1 = w0;
+      const uint32_t up = __shfl_up_sync(0xFFFFFFFFu, w1, 1);
+      const uint32_t p0 = lane ? up : last;
+      last = __shfl_sync(0xFFFFFFFFu, w1, 31);
       uint32_t u0 = ~__funnelshift_l(p0, w0, 1);
       uint32_t u1 = ~__funnelshift_l(p1, w1, 1);
-      c2 += step2<2>(p0, w0, p1, w1, u0, u1);
-      c3 += step2<3>(p0, w0, p1, w1, u0, u1);
-      c4 += step2<4>(p0, w0, p1, w1, u0, u1);
-      if (__any_sync(0xFFFFFFFFu, u0 | u1)) {
-        c5 += step2<5>(p0, w0, p1, w1, u0, u1);
-        SV_DEFER(i0, u0)
-        SV_DEFER(i1, u1)
-      }
+      U1 += __popc(u0) + __popc(u1);
+      step2<2>(p0, w0, p1, w1, u0, u1);
+      U2 += __popc(u0) + __popc(u1);
+      step2<3>(p0, w0, p1, w1, u0, u1);
+      U3 += __popc(u0) + __popc(u1);
+      step2<4>(p0, w0, p1, w1, u0, u1);
+      SV_K5(i0, i1)
     }
   } else
   for (uint32_t ib = mw + warp * 64u; ib < nwords; ib += nwarps * 64u) {
@@ -467,20 +493,24 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
     }
     const uint32_t w0 = a0 ? win[i0] : 0u, p0 = a0 ? win[i0 - 1] : 0u;
     const uint32_t w1 = a1 ? win[i1] : 0u, p1 = a1 ? win[i1 - 1] : 0u;
-    // k = 1..4 without votes: nearly every 64-word warp step needs k = 4
     uint32_t u0 = v0 & ~__funnelshift_l(p0, w0, 1);
     uint32_t u1 = v1 & ~__funnelshift_l(p1, w1, 1);
-    c2 += step2<2>(p0, w0, p1, w1, u0, u1);
-    c3 += step2<3>(p0, w0, p1, w1, u0, u1);
-    c4 += step2<4>(p0, w0, p1, w1, u0, u1);
-    if (__any_sync(0xFFFFFFFFu, u0 | u1)) {
-      c5 += step2<5>(p0, w0, p1, w1, u0, u1);
-      SV_DEFER(i0, u0)
-      SV_DEFER(i1, u1)
-    }
+    U1 += __popc(u0) + __popc(u1);
+    step2<2>(p0, w0, p1, w1, u0, u1);
+    U2 += __popc(u0) + __popc(u1);
+    step2<3>(p0, w0, p1, w1, u0, u1);
+    U3 += __popc(u0) + __popc(u1);
+    step2<4>(p0, w0, p1, w1, u0, u1);
+    SV_K5(i0, i1)
   }
+#undef SV_K5
 #undef SV_DEFER
   if (pend_u) finish_word(win, pend_i, pend_u, wstart + (int64_t)pend_i, a, sh);
+  // U_4 = c5t + x5: the k = 5 hits and the n left after k = 5
+  c2 += U1 - U2;
+  c3 += U2 - U3;
+  c4 += U3 - c5t - x5;
+  c5 += c5t;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
@@ -558,7 +588,7 @@ __device__ __forceinline__ void chunk_range(uint32_t j, uint32_t total, uint32_t
 // 2: general scan with the per-n output.  NS: number of stamped primes.
 template <int MODE, int NS>
 __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
-  extern __shared__ uint32_t win[];
+  extern __shared__ __align__(16) uint32_t win[];  // 16-byte aligned: the scan reads word pairs
   __shared__ ScanShared sh;
   __shared__ uint32_t stab[StampTab<NS>::kSize];
   constexpr bool LEAN = (MODE == 0);
