@@ -45,13 +45,12 @@ void Workspace::release_all() {
 }
 
 uint64_t host_isqrt(uint64_t x) {
-  // floor(sqrt(x)) by Newton's iteration from above (integer only)
-  if (x < 2) return x;
-  uint64_t r = x, y = x / 2 + 1;
-  while (y < r) {
-    r = y;
-    y = (r + x / r) / 2;
-  }
+  // floor(sqrt(x)): a double-precision estimate, made exact by integer steps
+  // (r^2 <= x < (r+1)^2 checked without overflow: r < 2^32)
+  uint64_t r = (uint64_t)std::sqrt((double)x);
+  if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
+  while (r > 0 && r * r > x) --r;
+  while (r < 0xFFFFFFFFull && (r + 1) * (r + 1) <= x) ++r;
   return r;
 }
 
@@ -79,7 +78,12 @@ uint32_t ilog2_u32(uint32_t x) { return 31u - (uint32_t)__builtin_clz(x); }
 // Number of table primes p with p <= x.
 uint32_t primes_upto(const sv_ctx *c, uint64_t x) {
   if (x > 0xFFFFFFFFull) x = 0xFFFFFFFFull;
-  return (uint32_t)(std::upper_bound(c->h_p.begin(), c->h_p.end(), (uint32_t)x) - c->h_p.begin());
+  // the index narrows the search to the primes of x's block of 2^kPiBlockLog2
+  const uint64_t blk = x >> kPiBlockLog2;
+  if (blk + 1 >= c->h_pi.size())
+    return (uint32_t)(std::upper_bound(c->h_p.begin(), c->h_p.end(), (uint32_t)x) - c->h_p.begin());
+  const auto b = c->h_p.begin();
+  return (uint32_t)(std::upper_bound(b + c->h_pi[blk], b + c->h_pi[blk + 1], (uint32_t)x) - b);
 }
 
 // Defaults and validation of the tuning knobs.
@@ -957,6 +961,12 @@ sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
   c->n_primes = n;
   c->n_div = n_div;
   c->h_p.swap(hp);
+  // h_pi[b]: the number of table primes below b * 2^kPiBlockLog2
+  c->h_pi.assign((pmax >> kPiBlockLog2) + 2, 0u);
+  for (size_t b = 0, j = 0; b < c->h_pi.size(); ++b) {
+    while (j < c->h_p.size() && ((uint64_t)c->h_p[j] >> kPiBlockLog2) < b) ++j;
+    c->h_pi[b] = (uint32_t)j;
+  }
   // suffix sums of 1/p^2 (sizing of the tile buckets, host only)
   c->inv_sq_suffix.assign(c->h_p.size() + 1, 0.0);
   for (size_t j = c->h_p.size(); j-- > 0;)

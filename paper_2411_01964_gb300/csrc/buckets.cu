@@ -138,26 +138,31 @@ __device__ void fill_barrett_item(const BucketArgs &a, FillReq *s_req, uint32_t 
 
 // ---- multiplier items -------------------------------------------------------
 
-// floor(sqrt(x)) by Newton's iteration from above (integer only).
-__device__ __forceinline__ uint64_t isqrt_floor(uint64_t x) {
-  if (x < 2) return x;
-  const int bits = 64 - __clzll((long long)x);
-  uint64_t r = 1ull << ((bits + 1) >> 1);  // >= sqrt(x)
-  for (;;) {
-    const uint64_t y = (r + x / r) >> 1;
-    if (y >= r) return r;
-    r = y;
-  }
+// j p^2 <= x, exactly (p < 2^32, so p^2 fits 64 bits; the product with j is
+// checked for overflow).
+__device__ __forceinline__ bool jsq_le(uint64_t j, uint64_t p, uint64_t x) {
+  const uint64_t p2 = p * p;
+  return __umul64hi(j, p2) == 0 && j * p2 <= x;
+}
+
+// floor(sqrt(floor(x / j))) for j >= 1, i.e. the largest r < 2^32 with
+// j r^2 <= x: a single-precision estimate of sqrt(x / j), then exact integer
+// steps (a few for the r < 2^26 of the prime table).
+__device__ __forceinline__ uint64_t isqrt_div(uint64_t x, uint64_t j) {
+  const float e = sqrtf((float)x / (float)j);
+  uint64_t r = e >= 4294967295.0f ? 0xFFFFFFFFull : (uint64_t)e;
+  while (r > 0 && !jsq_le(j, r, x)) --r;
+  while (r < 0xFFFFFFFFull && jsq_le(j, r + 1, x)) ++r;
+  return r;
 }
 
 // Bitmap bits [b0, b1] ((p-1)/2) of the odd p >= ph, p <= p_top, with an odd
 // multiple j p^2 in [mlo, mhi]; false if there are none.  An odd multiple
-// m = j p^2 lies in [mlo, mhi] exactly when
-// ceil(sqrt(ceil(mlo/j))) <= p <= floor(sqrt(floor(mhi/j))).
+// m = j p^2 lies in [mlo, mhi] exactly when j p^2 >= mlo and j p^2 <= mhi:
+// p > isqrt_div(mlo - 1, j) and p <= isqrt_div(mhi, j).
 __device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t j, uint64_t ph, uint64_t p_top,
                                            uint64_t *b0, uint64_t *b1) {
-  const uint64_t lq = (mlo + j - 1) / j, hq = mhi / j;
-  uint64_t plo = isqrt_floor(lq - 1) + 1, phi = isqrt_floor(hq);
+  uint64_t plo = isqrt_div(mlo - 1, j) + 1, phi = isqrt_div(mhi, j);
   if (plo < ph) plo = ph;
   if (phi > p_top) phi = p_top;
   if (plo > phi) return false;

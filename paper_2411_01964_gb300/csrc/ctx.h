@@ -13,6 +13,8 @@
 
 namespace sv {
 
+constexpr int kPiBlockLog2 = 12;  // block size of the host prime-count index
+
 // Growable device / pinned-host buffer (grows geometrically, never shrinks).
 template <class T, bool PINNED>
 struct Buf {
@@ -127,6 +129,7 @@ struct sv_ctx {
   uint64_t pbits_words = 0;
   uint32_t n_primes = 0, n_div = 0;
   std::vector<uint32_t> h_p;
+  std::vector<uint32_t> h_pi;  // h_pi[b] = number of h_p entries below b * 2^kPiBlockLog2
   std::vector<double> inv_sq_suffix;  // sum over j >= i of 1/p_j^2 (bucket sizing only)
   std::atomic<size_t> smem_set{0};  // dynamic smem the tile kernel was configured for
   sv::Workspace ws;
