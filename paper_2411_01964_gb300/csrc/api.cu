@@ -148,8 +148,9 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   if (il < g.i_dense) il = g.i_dense;
   if (il > g.i_dense + (uint32_t)kMaxSparsePrimes) il = g.i_dense + (uint32_t)kMaxSparsePrimes;
   g.i_large = il;
-  // primes >= 2^20 reach the buckets by enumerating multipliers (bucket_fill_j_kernel)
-  uint32_t ih = primes_upto(c, (1u << 20) - 1);
+  // primes >= 2^kMultPrimeLog2 reach the buckets by enumerating their odd
+  // multipliers (the multiplier items of bucket_fill_kernel)
+  uint32_t ih = primes_upto(c, (1u << kMultPrimeLog2) - 1);
   if (ih < il) ih = il;
   g.i_hyb = ih;
   g.p_hyb = ih < c->n_primes ? c->h_p[ih] : 0xFFFFFFFFu;

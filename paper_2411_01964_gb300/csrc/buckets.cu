@@ -195,11 +195,12 @@ __device__ __forceinline__ uint32_t interval_word(const BucketArgs &a, uint64_t 
 
 // Slice s of nsl of range r's odd multipliers j (j p^2 in the range, p >= p_hyb).
 // The smallest multipliers have the longest p intervals (and the most hits).
-// A long range (>= 2^30 odd numbers) spreads their bitmap words over the
-// threads of all slices, j by j, with the intervals computed once per item;
+// A long range (>= 2^30 odd numbers) spreads the bitmap words of all its
+// small multipliers over the threads of all slices, one word each (the
+// intervals and their word counts are computed once per item);
 // a shorter one gives each small j to one warp, lanes striding over words.
 // Larger j take one thread each.
-__device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[2], uint32_t s, uint32_t nsl, uint32_t r) {
+__device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_t s, uint32_t nsl, uint32_t r) {
   const Geometry &g = a.g;
   const ReqDesc &R = a.reqs[r];
   if (R.n_tiles == 0 || R.n_primes <= g.i_hyb) return;  // uniform over the block
@@ -213,20 +214,36 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[2], uint32_
   const uint64_t w_end = a.pt.bits_words;
   if (E - A >= (1ull << 30)) {
     __syncthreads();  // s_iv holds the previous item's intervals
-    if (threadIdx.x < kWarpJ) {
-      const uint64_t j = 2 * threadIdx.x + 1;
-      uint64_t b0 = 1, b1 = 0;
-      if (j > jmax || !p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) b0 = 1, b1 = 0;
-      s_iv[threadIdx.x][0] = b0;
-      s_iv[threadIdx.x][1] = b1;
+    if (threadIdx.x < kWarpJ) {  // warp 0: one small multiplier per lane
+      const uint32_t t = threadIdx.x;
+      const uint64_t j = 2 * t + 1;
+      uint64_t b0 = 1, b1 = 0, nw = 0;
+      if (j <= jmax && p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) {
+        const uint64_t w_last = min(b1 >> 5, w_end - 1);
+        if (w_last >= (b0 >> 5)) nw = w_last - (b0 >> 5) + 1;
+      }
+      uint64_t incl = nw;  // the words of multipliers 0 .. t
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (t >= (uint32_t)o) incl += y;
+      }
+      s_iv[t][0] = b0;
+      s_iv[t][1] = b1;
+      s_iv[t][2] = incl - nw;
+      if (t == kWarpJ - 1) s_iv[kWarpJ][2] = incl;
     }
     __syncthreads();
-    const uint64_t gx = (uint64_t)s * blockDim.x + threadIdx.x, nx = (uint64_t)nsl * blockDim.x;
-    for (uint32_t t = 0; t < kWarpJ; ++t) {
+    // the words of all small multipliers, one per thread of the item's slices
+    const uint64_t total = s_iv[kWarpJ][2];
+    for (uint64_t gw = (uint64_t)s * blockDim.x + threadIdx.x; gw < total; gw += (uint64_t)nsl * blockDim.x) {
+      uint32_t t = 0;  // the last multiplier whose words start at or below gw
+#pragma unroll
+      for (uint32_t h = kWarpJ / 2; h > 0; h >>= 1)
+        if (t + h < kWarpJ && s_iv[t + h][2] <= gw) t += h;
       const uint64_t b0 = s_iv[t][0], b1 = s_iv[t][1];
-      if (b1 < b0) continue;
-      const uint64_t w_last = min(b1 >> 5, w_end - 1);
-      for (uint64_t w = (b0 >> 5) + gx; w <= w_last; w += nx) emit_word(a, R, interval_word(a, w, b0, b1), w, 2 * t + 1);
+      const uint64_t w = (b0 >> 5) + (gw - s_iv[t][2]);
+      emit_word(a, R, interval_word(a, w, b0, b1), w, 2 * t + 1);
     }
   } else {
     const uint32_t lane = threadIdx.x & 31u;
@@ -265,7 +282,7 @@ struct FillItems {
 
 __global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_kernel(BucketArgs a, FillItems fi) {
   __shared__ FillReq s_req[kFillReqChunk];
-  __shared__ uint64_t s_iv[kWarpJ][2];
+  __shared__ uint64_t s_iv[kWarpJ + 1][3];  // small multipliers: interval bits, first word's rank; [kWarpJ][2]: total
   const Geometry &g = a.g;
   const uint32_t n_reqs = a.hdr->n_reqs;
   const uint32_t max_primes = a.hdr->max_primes;
@@ -302,7 +319,9 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
   fi.px = (uint32_t)std::min<uint64_t>((n_large_max + kFillThreads - 1) / kFillThreads, 4096);
   fi.py = std::min<uint32_t>((n_reqs + kFillReqChunk - 1) / kFillReqChunk, 64);
   const bool mult = a.g.p_hyb != 0xFFFFFFFFu && j_max != 0;
-  fi.jx = mult ? (uint32_t)std::min<uint64_t>((j_max / 2 + kFillThreads) / kFillThreads, 64) : 0u;
+  // slices: one thread per odd multiplier (at least eight slices, so that a
+  // long range's small-multiplier words spread over 2048 threads)
+  fi.jx = mult ? (uint32_t)std::min<uint64_t>(std::max<uint64_t>((j_max / 2 + kFillThreads) / kFillThreads, 8), 64) : 0u;
   fi.jy = mult ? std::min<uint32_t>(n_reqs, 1024) : 0u;
   const uint64_t items = (uint64_t)fi.px * fi.py + (uint64_t)fi.jx * fi.jy;
   const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(items, max_blocks ? max_blocks : 1));
