@@ -272,8 +272,8 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_
   }
 }
 
-// The item space: px prime blocks x py request chunks of Barrett items, then
-// jx slices x jy requests of multiplier items (host-chosen upper bounds).
+// The item space: jx slices x jy requests of multiplier items, then px prime
+// blocks x py request chunks of Barrett items (host-chosen upper bounds).
 // Each is trimmed to what the launch's header asks for, so that a captured
 // launch sized for its buffers wastes no block on absent work.
 struct FillItems {
