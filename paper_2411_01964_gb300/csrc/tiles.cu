@@ -754,8 +754,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       // a full window's strikes carry to the next window: its first struck
       // bit is the first one >= T, shifted down by T (q exceeds the margin,
       // so at most a few subtractions remain)
+      // (when some threads take one prime more than others, they are the last
+      // warps, whose dense tail is the lightest in the snake order)
       const bool carry = nwords == g.tw + g.mw;
-      for (uint32_t j = tid; j < n_sparse; j += S) {
+      for (uint32_t j = S - 1u - tid; j < n_sparse; j += S) {
         const uint32_t q = sh.sparse_q[j];
         uint32_t b = sh.sparse_off[j];
         for (; b < nbits; b += q) strike(win, b);
