@@ -75,3 +75,26 @@ def test_no_cpu_fallback_in_the_product_path():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "oracle.c" not in src, f
+
+
+def test_kernel_timing_argument(monkeypatch):
+    """sv_kernel_timing's binding: False is off, True every kernel (-1), a set of
+    kernel names their bit mask (bit i for kernel id i)."""
+    from paper_2411_01964_gb300 import binding
+
+    seen = []
+
+    class FakeLib:
+        def sv_kernel_timing(self, ctx, arg):
+            seen.append(arg)
+            return 0
+
+    monkeypatch.setattr(binding, "load", lambda *a, **k: FakeLib())
+    binding.sv_kernel_timing(None, False)
+    binding.sv_kernel_timing(None, True)
+    binding.sv_kernel_timing(None, ["tile"])
+    binding.sv_kernel_timing(None, ["init", "list_compact"])
+    ids = binding.KERNEL_IDS
+    assert seen == [0, -1, 1 << ids["tile"], (1 << ids["init"]) | (1 << ids["list_compact"])]
+    with pytest.raises(KeyError):
+        binding.sv_kernel_timing(None, ["no_such_kernel"])
