@@ -69,7 +69,10 @@ typedef struct sv_config {
                                     (6..tile_log2+1).  n - 2^k with 2^k <= W is read from the
                                     tile's own window; larger k go to the exact straggler test */
     uint32_t threads;            /* threads per CTA of the tile kernel (256, 512 or 1024) */
-    uint32_t large_prime_min;    /* primes p >= this are delivered through per-tile buckets */
+    uint32_t large_prime_min;    /* lower bound of the bucket threshold: primes from the threshold on
+                                    are delivered through per-tile buckets.  The library raises the
+                                    threshold to about sqrt(range length / 128) and keeps at most 2048
+                                    primes between the dense ones and it */
     uint32_t bucket_capacity;    /* entries per tile bucket (grown automatically on overflow) */
     uint32_t record_k_threshold; /* T: every n with mink(n) >= T is listed (default 6) */
     uint32_t ctas_per_sm;        /* resident tile CTAs per SM (1 or 2) */
