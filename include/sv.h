@@ -11,8 +11,12 @@
  * a histogram over k, first occurrences (the records of Table 3) and lists.
  *
  * Conventions shared by every entry point
- *   - All arithmetic is exact unsigned 64-bit integer arithmetic; no floating
- *     point is used anywhere on the GPU path.
+ *   - All arithmetic is exact unsigned 64-bit integer arithmetic: the device
+ *     code uses no floating point at all (square roots are integer Newton
+ *     iterations), and the host uses it only to estimate buffer sizes, which
+ *     never changes a result.
+ *   - Every entry point makes the context's CUDA device current while it runs
+ *     and gives the calling thread its own current device back afterwards.
  *   - squarefree(s): s >= 1 and no prime p with p^2 | s.  1 is squarefree.
  *   - mink(n) = min{ k >= 1 : 2^k < n and n - 2^k squarefree }.  If no such k
  *     exists n is a "failure" (the case Algorithm 2 prints as "no
@@ -265,9 +269,11 @@ sv_status sv_set_config(sv_ctx *ctx, const sv_config *cfg);
 sv_status sv_last_transfer(const sv_ctx *ctx, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
 
 /*
- * sv_verify_range for callers that cannot allocate memory when they verify:
- * code running while a CUDA graph is captured (cudaMalloc is not allowed
- * then), real-time loops that must not reach the allocator, processes whose
+ * sv_verify_range for callers that cannot allocate memory when they verify.
+ * Such callers include a process whose GPU memory is already held by a caching
+ * allocator (PyTorch's, for one), where a cudaMalloc by this library would
+ * fail; latency-critical loops, because cudaMalloc and cudaFree can
+ * synchronise the whole device and take milliseconds; and services whose
  * memory budget is fixed at start-up.  The paper has no counterpart: this is
  * a property of this library's interface, not of the method.
  *
@@ -278,13 +284,18 @@ sv_status sv_last_transfer(const sv_ctx *ctx, uint64_t *h2d_bytes, uint64_t *d2h
  * from one fixed 8 MiB array in device memory that the library declares at
  * file scope; every GPU that loads the library holds those 8 MiB until the
  * process exits.  Results are written into the caller's buffers in *out
- * (HOST memory, as for sv_verify_range).
+ * (HOST memory, as for sv_verify_range).  The call blocks: it waits for the
+ * context's stream and copies the results back through small host stack
+ * buffers before it returns.
  *
  * Limits and rules:
  *   - hi - lo <= 2^32, and the range's tile buckets must fit the array (true
  *     for every such range with the default tile size); otherwise SV_ERANGE.
- *   - At most 65536 listed n (mink >= T) and 1024 failures per call; more
- *     listed n gives SV_EOVERFLOW.  out->per_n_k must be NULL (SV_EINVAL).
+ *   - At most 65536 listed n (mink >= T) and 1024 failures per call, and a
+ *     straggler queue (n whose n - 2^k leaves a tile's look-back window) of
+ *     at least 4096 entries: what the array holds after the other parts.  More
+ *     listed n or more stragglers give SV_EOVERFLOW (sv_verify_range would
+ *     grow its buffers instead).  out->per_n_k must be NULL (SV_EINVAL).
  *   - sv_init_primes must have been called before (it allocates, once, at
  *     set-up): SV_ENOPRIMES otherwise.
  *   - The first call on each device looks up the array's device address

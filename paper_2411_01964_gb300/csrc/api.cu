@@ -45,13 +45,24 @@ void Workspace::release_all() {
 }
 
 uint64_t host_isqrt(uint64_t x) {
-  // floor(sqrt(x)): a double-precision estimate, made exact by integer steps
-  // (r^2 <= x < (r+1)^2 checked without overflow: r < 2^32)
-  uint64_t r = (uint64_t)std::sqrt((double)x);
-  if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
-  while (r > 0 && r * r > x) --r;
-  while (r < 0xFFFFFFFFull && (r + 1) * (r + 1) <= x) ++r;
-  return r;
+  // floor(sqrt(x)) by Newton's iteration from above, integer only: the start
+  // 2^ceil(bits/2) is at least the root, and the iterates fall to it
+  if (x < 2) return x;
+  const int bits = 64 - __builtin_clzll(x);
+  uint64_t r = 1ull << ((bits + 1) / 2);
+  for (;;) {
+    const uint64_t y = (r + x / r) / 2;
+    if (y >= r) return r;
+    r = y;
+  }
+}
+
+// The square roots of the bucket fill's odd-multiple interval ends (ReqDesc).
+void set_interval_roots(ReqDesc &d, uint32_t mw) {
+  const int64_t ws = d.w0 - (int64_t)mw;
+  const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
+  d.sq_lo = (uint32_t)host_isqrt(2 * A);
+  d.sq_hi = d.jhi ? (uint32_t)host_isqrt(2 * d.jhi - 1) : 0u;
 }
 
 uint64_t range_odd_count(uint64_t lo, uint64_t hi) {
@@ -72,6 +83,11 @@ sv_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SV_OK : SV_ECUD
     cudaError_t e__ = (expr);                   \
     if (e__ != cudaSuccess) return SV_ECUDA;    \
   } while (0)
+
+// The context's device is current until the end of the enclosing entry point.
+#define SV_ON_DEVICE(c)                       \
+  DevGuard dev_guard__((c)->device);          \
+  if (!dev_guard__.ok) return SV_ECUDA
 
 uint32_t ilog2_u32(uint32_t x) { return 31u - (uint32_t)__builtin_clz(x); }
 
@@ -236,6 +252,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
     d.fail_cap = s.fail_cap;
     fail_total += s.fail_cap;
     d.sieve_only = s.sieve_only ? 1u : 0u;
+    set_interval_roots(d, g.mw);
     d.bitmap_out = s.bitmap_out;
     ws.h_reqs.p[r] = d;
   }
@@ -901,6 +918,7 @@ sv_status sv_create(sv_ctx **out, const sv_config *cfg) {
 
 void sv_destroy(sv_ctx *c) {
   if (!c) return;
+  DevGuard dev_guard__(c->device);
   if (c->server) server_destroy(c->server);
   c->server = nullptr;
   cudaStreamSynchronize(c->stream);
@@ -928,6 +946,7 @@ sv_status sv_get_config(const sv_ctx *c, sv_config *out) {
 sv_status sv_init_primes(sv_ctx *c, uint64_t max_hi) {
   if (!c) return SV_EINVAL;
   if (max_hi > kMaxHi) return SV_ERANGE;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if (c->d_p && max_hi <= c->max_hi) return SV_OK;
   const uint64_t pmax = host_isqrt(max_hi > 1 ? max_hi - 1 : 1);
@@ -996,6 +1015,7 @@ sv_status sv_verify_range(sv_ctx *c, uint64_t lo, uint64_t hi, sv_range_result *
   if (s) return s;
   if (!out) return SV_EINVAL;
   if ((s = check_range(c, lo, hi))) return s;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   std::vector<RangeSpec> specs(1);
   specs[0].lo = lo;
@@ -1026,6 +1046,7 @@ sv_status sv_verify_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, siz
   if (count && (!lo || !hi || !out)) return SV_EINVAL;
   for (size_t i = 0; i < count; ++i)
     if ((s = check_range(c, lo[i], hi[i]))) return s;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   std::vector<RangeSpec> specs(count);
   std::vector<sv_range_result *> outs(count);
@@ -1046,6 +1067,7 @@ sv_status sv_launch_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, siz
   if (count == 0 || !lo || !hi) return SV_EINVAL;
   for (size_t i = 0; i < count; ++i)
     if ((s = check_range(c, lo[i], hi[i]))) return s;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if ((s = ensure_tile_smem(c))) return s;
   std::vector<RangeSpec> specs(count);
@@ -1068,6 +1090,7 @@ sv_status sv_launch_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, siz
 
 sv_status sv_fetch_batch(sv_ctx *c, sv_range_result *out, size_t count) {
   if (!c || (count && !out)) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if (!c->pending || count != c->pending_specs.size()) return SV_EINVAL;
   c->pending = false;
@@ -1090,6 +1113,7 @@ sv_status sv_min_k(sv_ctx *c, const uint64_t *points, size_t count, uint8_t *out
   sv_status s = check_ready(c);
   if (s) return s;
   if (count && (!points || !out_k)) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   return run_points(c, points, count, out_k, c->stream, c->ws);
 }
@@ -1099,6 +1123,7 @@ sv_status sv_min_k_device(sv_ctx *c, const uint64_t *d_points, size_t count, uin
   if (s) return s;
   if (count && (!d_points || !d_out_k)) return SV_EINVAL;
   if (count == 0) return SV_OK;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   uint64_t grid = ((uint64_t)count * 32 + 255) / 256;
   const uint64_t gmax = (uint64_t)c->num_sms * 8;
@@ -1115,6 +1140,7 @@ sv_status sv_sieve_bitmap(sv_ctx *c, uint64_t lo, uint64_t hi, uint32_t *d_bitma
   if ((s = check_range(c, lo, hi))) return s;
   if (sv_bitmap_words(lo, hi) == 0) return SV_OK;
   if (!d_bitmap) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   std::vector<RangeSpec> specs(1);
   specs[0].lo = lo;
@@ -1128,6 +1154,7 @@ sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_
   sv_status s = check_ready(c);
   if (s) return s;
   if ((s = check_range(c, lo, hi))) return s;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if ((s = ensure_tile_smem(c))) return s;
   std::vector<RangeSpec> specs(1);
@@ -1147,6 +1174,7 @@ sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_
 
 sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
   if (!c || !out) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if (!c->pending || c->pending_specs.size() != 1) return SV_EINVAL;
   c->pending = false;
@@ -1170,6 +1198,7 @@ sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
 
 sv_status sv_synchronize(sv_ctx *c) {
   if (!c) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   return cuda_status(cudaStreamSynchronize(c->stream));
 }
 
@@ -1186,6 +1215,7 @@ uint64_t sv_kernel_launches(const sv_ctx *c) { return c ? c->launches.load() : 0
 
 sv_status sv_kernel_timing(sv_ctx *c, int enable) {
   if (!c) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SV_ECUDA;
   for (auto &k : c->kev) {
@@ -1203,6 +1233,7 @@ sv_status sv_kernel_timing(sv_ctx *c, int enable) {
 
 sv_status sv_kernel_time(sv_ctx *c, int kernel, double *total_ms, uint64_t *launches) {
   if (!c || kernel < 0 || kernel >= 8) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SV_ECUDA;
   for (auto &k : c->kev) {
@@ -1237,6 +1268,7 @@ sv_status sv_autotune(sv_ctx *c, uint64_t lo, uint64_t hi, sv_config *chosen) {
   sv_status s = check_ready(c);
   if (s) return s;
   if ((s = check_range(c, lo, hi))) return s;
+  SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
   const sv_config base = c->cfg;
   sv_config best = base;
@@ -1299,6 +1331,7 @@ sv_status sv_submit(sv_ctx *c, const sv_request *req, uint64_t *ticket) {
   sv_status s = check_ready(c);
   if (s) return s;
   if (!req || !ticket) return SV_EINVAL;
+  SV_ON_DEVICE(c);
   {
     std::lock_guard<std::mutex> lk(c->mu);
     if (!c->server) c->server = server_create(c);

@@ -145,12 +145,30 @@ __device__ __forceinline__ bool jsq_le(uint64_t j, uint64_t p, uint64_t x) {
   return __umul64hi(j, p2) == 0 && j * p2 <= x;
 }
 
-// floor(sqrt(floor(x / j))) for j >= 1, i.e. the largest r < 2^32 with
-// j r^2 <= x: a single-precision estimate of sqrt(x / j), then exact integer
-// steps (a few for the r < 2^26 of the prime table).
-__device__ __forceinline__ uint64_t isqrt_div(uint64_t x, uint64_t j) {
-  const float e = sqrtf((float)x / (float)j);
-  uint64_t r = e >= 4294967295.0f ? 0xFFFFFFFFull : (uint64_t)e;
+// z ~ 2^63 / sqrt(j) for j >= 1 (integer fixed point), by Newton's iteration
+// for the reciprocal square root, z <- z (3 - j z^2) / 2, which needs no
+// division.  The start is 0.85 or 0.6 times 2^(63 - h) for j in [4^h, 2 4^h)
+// or [2 4^h, 4^(h+1)): within 20% of the root, from where five steps reach a
+// relative error far below 2^-40.  Only an estimate: callers correct it
+// exactly.
+__device__ __forceinline__ uint64_t rsqrt_fix(uint64_t j) {
+  const uint32_t b = 64u - (uint32_t)__clzll((long long)j);
+  const uint32_t h = (b - 1u) >> 1;
+  uint64_t z = (((b - 1u) & 1u) ? 0x4CCCCCCCCCCCCCCCull : 0x6CCCCCCCCCCCCCCCull) >> h;
+#pragma unroll
+  for (int it = 0; it < 5; ++it) {
+    const uint64_t u = j * __umul64hi(z, z);  // j z^2 / 2^64, about 2^62
+    z = __umul64hi(z, (3ull << 62) - u) << 1;
+  }
+  return z;
+}
+
+// floor(sqrt(floor(x / j))), i.e. the largest r < 2^32 with j r^2 <= x, from
+// S = floor(sqrt(x)) and z = rsqrt_fix(j): the estimate S z / 2^63 lies within
+// one of the result, and exact integer steps finish it.
+__device__ __forceinline__ uint64_t isqrt_div(uint64_t x, uint64_t S, uint64_t z, uint64_t j) {
+  uint64_t r = __umul64hi(S << 1, z);
+  if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
   while (r > 0 && !jsq_le(j, r, x)) --r;
   while (r < 0xFFFFFFFFull && jsq_le(j, r + 1, x)) ++r;
   return r;
@@ -159,10 +177,12 @@ __device__ __forceinline__ uint64_t isqrt_div(uint64_t x, uint64_t j) {
 // Bitmap bits [b0, b1] ((p-1)/2) of the odd p >= ph, p <= p_top, with an odd
 // multiple j p^2 in [mlo, mhi]; false if there are none.  An odd multiple
 // m = j p^2 lies in [mlo, mhi] exactly when j p^2 >= mlo and j p^2 <= mhi:
-// p > isqrt_div(mlo - 1, j) and p <= isqrt_div(mhi, j).
-__device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t j, uint64_t ph, uint64_t p_top,
-                                           uint64_t *b0, uint64_t *b1) {
-  uint64_t plo = isqrt_div(mlo - 1, j) + 1, phi = isqrt_div(mhi, j);
+// p > isqrt_div(mlo - 1, j) and p <= isqrt_div(mhi, j).  sq_lo and sq_hi are
+// floor(sqrt(mlo - 1)) and floor(sqrt(mhi)), computed once per range.
+__device__ __forceinline__ bool p_interval(uint64_t mlo, uint64_t mhi, uint64_t sq_lo, uint64_t sq_hi, uint64_t j,
+                                           uint64_t ph, uint64_t p_top, uint64_t *b0, uint64_t *b1) {
+  const uint64_t z = rsqrt_fix(j);
+  uint64_t plo = isqrt_div(mlo - 1, sq_lo, z, j) + 1, phi = isqrt_div(mhi, sq_hi, z, j);
   if (plo < ph) plo = ph;
   if (phi > p_top) phi = p_top;
   if (plo > phi) return false;
@@ -218,7 +238,7 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_
       const uint32_t t = threadIdx.x;
       const uint64_t j = 2 * t + 1;
       uint64_t b0 = 1, b1 = 0, nw = 0;
-      if (j <= jmax && p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) {
+      if (j <= jmax && p_interval(mlo, mhi, R.sq_lo, R.sq_hi, j, ph, p_top, &b0, &b1)) {
         const uint64_t w_last = min(b1 >> 5, w_end - 1);
         if (w_last >= (b0 >> 5)) nw = w_last - (b0 >> 5) + 1;
       }
@@ -251,7 +271,7 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_
     for (uint64_t t = (uint64_t)s * wpb + (threadIdx.x >> 5); t < kWarpJ && 2 * t + 1 <= jmax; t += (uint64_t)nsl * wpb) {
       const uint64_t j = 2 * t + 1;
       uint64_t b0, b1;
-      if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+      if (!p_interval(mlo, mhi, R.sq_lo, R.sq_hi, j, ph, p_top, &b0, &b1)) continue;
       const uint64_t w_last = min(b1 >> 5, w_end - 1);
       for (uint64_t w = (b0 >> 5) + lane; w <= w_last; w += 32) emit_word(a, R, interval_word(a, w, b0, b1), w, j);
     }
@@ -260,7 +280,7 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_
        t += (uint64_t)nsl * blockDim.x) {
     const uint64_t j = 2 * t + 1;
     uint64_t b0, b1;
-    if (!p_interval(mlo, mhi, j, ph, p_top, &b0, &b1)) continue;
+    if (!p_interval(mlo, mhi, R.sq_lo, R.sq_hi, j, ph, p_top, &b0, &b1)) continue;
     const uint64_t w_last = min(b1 >> 5, w_end - 1);
     for (uint64_t wd = b0 >> 5; wd <= w_last; wd += 4) {  // four words in flight
       uint32_t m[4];

@@ -111,6 +111,29 @@ struct Workspace {
 
 class Server;  // serving loop (server.cu)
 
+// Makes the context's device current for the length of an entry point and
+// gives the calling thread its own device back afterwards, so that a call from
+// a thread that has another GPU current still works on the context's GPU.
+struct DevGuard {
+  int prev = -1;
+  bool switched = false, ok = true;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev) {
+      switched = cudaSetDevice(dev) == cudaSuccess;
+      ok = switched;
+    }
+  }
+  ~DevGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+  DevGuard(const DevGuard &) = delete;
+  DevGuard &operator=(const DevGuard &) = delete;
+};
+
 }  // namespace sv
 
 struct sv_ctx {
@@ -168,7 +191,7 @@ sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_rang
 // Points already staged in ws.h_points: upload, test, download into
 // ws.h_points_out (no wait).
 sv_status launch_points_async(sv_ctx *c, uint64_t count, Workspace &ws, cudaStream_t st);
-uint64_t host_isqrt(uint64_t x);
+void set_interval_roots(ReqDesc &d, uint32_t mw);
 uint64_t range_odd_count(uint64_t lo, uint64_t hi);
 // Device list entries to reserve for a range of n_odd odd n with threshold T
 // (twice the heuristic expectation plus slack, at most cap); an overflow is

@@ -1,15 +1,18 @@
 // noalloc.cu -- sv_verify_range_noalloc: sv_verify_range without any allocation.
 //
-// Some callers cannot allocate device memory at the point where they verify a
-// range: code that runs while a CUDA graph is being captured (cudaMalloc is
-// not allowed then), real-time loops that must not hit the allocator's
-// synchronisation, and hosts whose memory budget is fixed at start-up.  This
-// entry point runs the same kernels as sv_verify_range, but every piece of
-// scratch memory they need (launch header, range descriptor, result slot,
-// tile buckets, straggler queue, list and failure arenas) is carved out of one
-// file-scope __device__ array of kScratchBytes.  It calls no cudaMalloc,
-// cudaFree, cudaMallocHost or other allocating routine; results are copied
-// into the caller's own buffers through small stack arrays.
+// Some callers cannot allocate memory at the point where they verify a range:
+// a process that shares the GPU with a caching allocator (PyTorch's, for one)
+// that has already reserved nearly all device memory, so that a cudaMalloc by
+// this library would fail; latency-critical loops, because cudaMalloc and
+// cudaFree can synchronise the whole device and take milliseconds; and
+// services whose memory budget is fixed when they start.  This entry point
+// runs the same kernels as sv_verify_range, but every piece of scratch memory
+// they need (launch header, range descriptor, result slot, tile buckets,
+// straggler queue, list and failure arenas) is carved out of one file-scope
+// __device__ array of kScratchBytes.  It calls no cudaMalloc, cudaFree,
+// cudaMallocHost or other allocating routine; results are copied into the
+// caller's own buffers through small stack arrays.  The call blocks: it
+// waits for the context's stream before it returns.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -21,7 +24,7 @@ namespace sv {
 namespace {
 
 constexpr size_t kScratchBytes = 8u << 20;  // 8 MiB, held by every GPU that loads the library
-constexpr uint32_t kNaStrag = 4096;         // straggler queue entries
+constexpr uint32_t kNaStragMin = 4096;      // straggler queue entries at least (the rest of the array)
 constexpr uint32_t kNaList = 65536;         // listed n (mink >= T) per call
 constexpr uint32_t kNaFail = 1024;          // failures kept per call
 constexpr int kMaxDevices = 64;
@@ -36,7 +39,8 @@ unsigned char *g_scratch_addr[kMaxDevices];  // device address of the array, per
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t hdr, req, slot, strag, list_n, list_k, fail, bcount, bdata, end;
+  size_t hdr, req, slot, list_n, list_k, fail, bcount, bdata, strag, end;
+  uint32_t strag_cap;  // the straggler queue takes what the other parts leave
 };
 
 Layout make_layout(uint32_t n_tiles, uint32_t cap) {
@@ -48,8 +52,6 @@ Layout make_layout(uint32_t n_tiles, uint32_t cap) {
   o = up256(o + sizeof(ReqDesc));
   L.slot = o;
   o = up256(o + sizeof(ResultSlot));
-  L.strag = o;
-  o = up256(o + sizeof(Straggler) * kNaStrag);
   L.list_n = o;
   o = up256(o + sizeof(uint64_t) * kNaList);
   L.list_k = o;
@@ -60,14 +62,21 @@ Layout make_layout(uint32_t n_tiles, uint32_t cap) {
   o = up256(o + sizeof(uint32_t) * (size_t)(n_tiles ? n_tiles : 1));
   L.bdata = o;
   o = up256(o + sizeof(uint32_t) * (size_t)(n_tiles ? n_tiles : 1) * cap);
-  L.end = o;
+  L.strag = o;
+  const size_t room = o < kScratchBytes ? (kScratchBytes - o) / sizeof(Straggler) : 0;
+  L.strag_cap = (uint32_t)(room < 0xFFFFFFFFull ? room : 0xFFFFFFFFull);
+  o = up256(o + sizeof(Straggler) * (size_t)kNaStragMin);
+  L.end = o;  // the layout fits when end <= kScratchBytes
   return L;
 }
 
-// The array's device address on the current device: looked up once per
-// device (cudaGetSymbolAddress with that device current), then reused.
+// The array's device address on device dev, which the caller has made
+// current: cudaGetSymbolAddress resolves the symbol on the current device.
+// Looked up once per device, then reused.
 sv_status scratch_base(int dev, unsigned char **out) {
   if (dev < 0 || dev >= kMaxDevices) return SV_EINVAL;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != dev) return SV_ECUDA;
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_addr[dev]) {
     void *p = nullptr;
@@ -166,6 +175,10 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
   if (out->per_n_k) return SV_EINVAL;  // a per-n output needs n_odd bytes: use sv_launch_range
   if (hi > (1ull << 62) || hi > c->max_hi) return SV_ERANGE;
   if (hi > lo && hi - lo > kMaxSpan) return SV_ERANGE;  // longer ranges need more scratch than the array has
+  // the context's device is current for the whole call (and the caller's
+  // own device afterwards), so the array's address is the one on that device
+  DevGuard dev_guard(c->device);
+  if (!dev_guard.ok) return SV_ECUDA;
   std::lock_guard<std::mutex> lk(c->mu);
   unsigned char *base = nullptr;
   sv_status s = scratch_base(c->device, &base);
@@ -189,6 +202,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
   const uint64_t nwords = (d.jhi > d.jlo) ? (uint64_t)(d.wend - d.w0) : 0;
   const uint64_t nt = (nwords + g.tw - 1) / g.tw;
   d.n_primes = hi > 1 ? primes_upto_of(c, host_isqrt(hi - 1)) : 0;
+  set_interval_roots(d, g.mw);
   d.list_cap = kNaList;
   d.fail_cap = kNaFail;
 
@@ -252,7 +266,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
     t.list_k = (uint8_t *)(base + L.list_k);
     t.fail_n = (uint64_t *)(base + L.fail);
     t.strag = (Straggler *)(base + L.strag);
-    t.strag_cap = kNaStrag;
+    t.strag_cap = L.strag_cap;
     t.bucket_count = d_bcount;
     t.bucket_data = d_bdata;
     uint32_t grid = (uint32_t)c->num_sms * c->cfg.ctas_per_sm;
@@ -271,7 +285,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
     sa.list_k = t.list_k;
     sa.fail_n = t.fail_n;
     sa.strag = t.strag;
-    sa.strag_cap = kNaStrag;
+    sa.strag_cap = L.strag_cap;
     sa.rec_t = g.rec_t;
     if (launch_stragglers(sa, (uint32_t)c->num_sms * 2, st) != cudaSuccess) return SV_ECUDA;
     c->launches++;

@@ -193,17 +193,6 @@ __global__ void compact_kernel(const uint32_t *bits, uint64_t nwords, const uint
   }
 }
 
-uint64_t isqrt_host(uint64_t x) {
-  // Newton's iteration from above, integer only.
-  if (x < 2) return x;
-  uint64_t r = x, y = (r + 1) / 2;
-  while (y < r) {
-    r = y;
-    y = (r + x / r) / 2;
-  }
-  return r;
-}
-
 }  // namespace
 
 // Builds the table of odd primes <= pmax (pmax < 2^32).  Device arrays are
@@ -218,7 +207,7 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
   *bits_words = 0;
   *n_out = *n_div_out = 0;
   if (pmax < 3) pmax = 3;
-  const uint64_t B = isqrt_host(pmax);
+  const uint64_t B = host_isqrt(pmax);
   const uint64_t nwords = (pmax / 2 + 1 + 31) / 32;
   const uint32_t nblocks = (uint32_t)((nwords + kCountWords - 1) / kCountWords);
   uint32_t *d_base = nullptr, *d_nbase = nullptr, *d_bits = nullptr, *d_counts = nullptr, *d_total = nullptr;

@@ -61,6 +61,10 @@ struct ReqDesc {
   uint64_t list_off, list_cap;  // this range's region of the list arena
   uint64_t fail_off, fail_cap;  // this range's region of the failure arena
   uint32_t sieve_only;  // 1: write the sieved words to bitmap_out, no scan
+  // floor(sqrt(2A)) and floor(sqrt(2E - 1)) for the window bits [A, E) the
+  // bucket fill covers (A = 32 max(w0 - mw, 0), E = jhi): the integer square
+  // roots of the ends of its odd-multiple interval, one per range
+  uint32_t sq_lo, sq_hi;
   uint32_t pad;
   uint32_t *bitmap_out; // sieve_only: word (a - w0) receives absolute word a
 };
@@ -193,6 +197,7 @@ size_t tile_static_smem();
 cudaError_t launch_stragglers(const StragArgs &a, uint32_t grid, cudaStream_t st);
 cudaError_t launch_points(PrimeTab pt, const uint64_t *pts, uint64_t count, uint8_t *out,
                           uint32_t grid, cudaStream_t st);
+uint64_t host_isqrt(uint64_t x);  // floor(sqrt(x)), integer only (host)
 cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, uint64_t **d_inv,
                               uint64_t **d_lim, uint32_t **d_bits, uint64_t *bits_words, uint32_t *n,
                               uint32_t *n_div, cudaStream_t st);

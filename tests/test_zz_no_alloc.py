@@ -1,9 +1,10 @@
 """sv_verify_range_noalloc: the verification entry point for callers that cannot
-allocate memory when they verify (for instance while a CUDA graph is being
-captured, or in loops that must not reach the allocator).  It must return
-exactly what sv_verify_range returns, on two calls in a row: every call reuses
-the library's one fixed scratch array, so the second call also checks that the
-first call's leftovers are cleared.
+allocate memory when they verify.  Examples are a process whose GPU memory is
+already held by another framework's caching allocator, where a cudaMalloc would
+fail, and latency-critical loops, where cudaMalloc and cudaFree could stall the
+device.  It must return exactly what sv_verify_range returns, on two calls in a
+row: every call reuses the library's one fixed scratch array, so the second
+call also checks that the first call's leftovers are cleared.
 
 This file is collected last, so a run that stops at the first failure has
 already run every other test."""
