@@ -282,24 +282,42 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(lo: int, hi: int, seconds_target: float, max_sample: int) -> dict:
+def cpu_baseline(lo: int, hi: int, seconds_target: float, max_sample: int):
+    """The oracle, as it stands, on all host cores over a bounded sample
+    [lo, lo + sample) sized for about seconds_target; returns the baseline
+    entry and the oracle's result (kept for the parity check)."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     # calibrate on a small piece, then size the sample for ~seconds_target
-    probe = min(hi - lo, 1 << 26)
+    probe = min(hi - lo, 1 << 28)
     t0 = time.perf_counter()
     oracle.verify_range(lo, lo + probe, threads=cores)
     dt = max(time.perf_counter() - t0, 1e-3)
     sample = int(probe * seconds_target / dt) & ~((1 << 20) - 1)
     sample = max(probe, min(sample, hi - lo, max_sample))
     t0 = time.perf_counter()
-    r = oracle.verify_range(lo, lo + sample, threads=cores)
+    r = oracle.verify_range(lo, lo + sample, threads=cores, list_cap=1 << 21)
     dt = time.perf_counter() - t0
     n = odd_count(lo, lo + sample)
+    whole = " (the whole workload)" if sample == hi - lo else ""
     return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"odd n of [{lo}, {lo + sample}) ({n} odd n, {dt:.1f} s), all host cores",
-            "n_odd": r.n_odd}
+            "sample": f"odd n of [{lo}, {lo + sample}){whole} ({n} odd n, {dt:.1f} s), all host cores",
+            "n_odd": r.n_odd}, r
+
+
+def parity_check(v, o) -> dict:
+    """The GPU result of the oracle's range [o.lo, o.hi) against the oracle's,
+    element by element (outside the timed region)."""
+    import numpy as np
+    g = v.verify_range(o.lo, o.hi, list_cap=1 << 21)
+    same = (g.n_odd == o.n_odd and g.hist == o.hist and g.first_n == o.first_n and g.ksum == o.ksum
+            and g.kmax == o.kmax and g.list_len == len(o.list_n) and not o.list_overflow
+            and bool(np.array_equal(g.list_n, o.list_n)) and bool(np.array_equal(g.list_k, o.list_k))
+            and g.fail_len == len(o.failures) and bool(np.array_equal(g.failures, o.failures)))
+    return {"equal": same, "range": [o.lo, o.hi], "odd_n": o.n_odd,
+            "compared": "hist, first_n, ksum, kmax, the whole ascending list (n, mink) with mink >= 6, failures",
+            "list_len": int(g.list_len), "ksum": int(g.ksum), "kmax": int(g.kmax)}
 
 
 def main() -> int:
@@ -310,7 +328,7 @@ def main() -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-sample", type=int, default=1 << 31)
     ap.add_argument("--tile-log2", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
@@ -465,7 +483,8 @@ def main() -> int:
                    "list_len": res.list_len},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(lo, hi, args.cpu_seconds, 1 << 34)
+        line["cpu_baseline"], o = cpu_baseline(lo, hi, args.cpu_seconds, hi - lo)
+        line["parity"] = parity_check(v, o)
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched"] = bench_batch(v, stream, flush, args.batch_requests)
     if rank == 0 and world == 1 and not args.no_serve:

@@ -169,6 +169,17 @@ sv_status sv_init_primes(sv_ctx *ctx, uint64_t max_hi);
 sv_status sv_prime_count(const sv_ctx *ctx, uint64_t *count, uint64_t *largest);
 
 /*
+ * Copies the resident table (the primes of Algorithm 1, Sec. 3) into HOST
+ * arrays owned by the caller, for inspection: p[i] (ascending odd primes) and
+ * mu[i] = floor((2^64-1) / p^2) for i < min(cap, count); inv[i] = p^-1 mod
+ * 2^64 and lim[i] = floor((2^64-1) / p) for i < min(cap, *n_div), the primes
+ * that carry divisibility constants (all p < 2^21 of the table).  Any array
+ * pointer may be NULL.  Blocking.  Errors: SV_EINVAL, SV_ENOPRIMES, SV_ECUDA.
+ */
+sv_status sv_prime_table_copy(sv_ctx *ctx, uint32_t *p, uint64_t *mu, uint64_t *inv, uint64_t *lim,
+                              uint64_t cap, uint64_t *n_div);
+
+/*
  * Verify one range (Algorithms 1 and 2, Sec. 3): mink of every odd n in
  * [max(lo,3), hi), aggregated into *out.  Blocking.  out's buffers are HOST
  * memory owned by the caller.  lo >= hi gives an empty result.

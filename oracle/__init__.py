@@ -83,6 +83,8 @@ def _load():
             lib.or_sieve_odd.restype = ctypes.c_int
             lib.or_verify_range.argtypes = [ctypes.POINTER(_Result), ctypes.c_int, u64, u64]
             lib.or_verify_range.restype = ctypes.c_int
+            lib.or_verify_ranges.argtypes = [ctypes.POINTER(_Result), ctypes.c_int64, ctypes.c_int, u64, u64]
+            lib.or_verify_ranges.restype = ctypes.c_int
             lib.or_verify_range_brute.argtypes = [ctypes.POINTER(_Result), ctypes.c_int]
             lib.or_verify_range_brute.restype = ctypes.c_int
             lib.or_min_k.argtypes = [u64p, u64, u8p]
@@ -209,3 +211,58 @@ def verify_range_brute(lo: int, hi: int, list_k_threshold: int = 6, list_cap: in
                        per_n: bool = False, threads: int = 0) -> RangeResult:
     """The definition: every n - 2^k decided by trial division (small ranges)."""
     return _run_range(lo, hi, list_k_threshold, list_cap, per_n, True, threads, 0, 0)
+
+
+# P(mink >= T) from Table 2 (Sec. 2), only to size list buffers: a range whose
+# list does not fit is run again with exact room.
+_TAIL = {1: 1.0, 2: 1.8943e-1, 3: 2.4129e-2, 4: 2.1482e-3, 5: 1.3902e-4, 6: 6.8527e-6, 7: 2.6694e-7}
+
+
+def verify_ranges(ranges, list_k_threshold: int = 6, threads: int = 0, margin: int = 1 << 16,
+                  chunk: int = 1 << 24) -> list:
+    """verify_range for each (lo, hi) of `ranges`, with one prime list shared by
+    all and whole ranges spread over the host cores (longest first)."""
+    lib = _load()
+    ranges = [(int(a), int(b)) for a, b in ranges]
+    count = len(ranges)
+    if count == 0:
+        return []
+    if threads <= 0:
+        threads = os.cpu_count() or 1
+    order = sorted(range(count), key=lambda i: -(ranges[i][1] - ranges[i][0]))
+    arr = (_Result * count)()
+    keep = []
+    tail = _TAIL.get(list_k_threshold, 1.0 if list_k_threshold < 1 else 1e-7)
+    for slot, i in enumerate(order):
+        lo, hi = ranges[i]
+        nlo = max(lo, 3) | 1
+        n_odd = (hi - nlo + 1) // 2 if hi > nlo else 0
+        cap = int(4 * tail * n_odd) + 1024
+        lst = np.zeros(cap, dtype=np.uint64)
+        lstk = np.zeros(cap, dtype=np.uint8)
+        fails = np.zeros(64, dtype=np.uint64)
+        r = arr[slot]
+        r.lo, r.hi, r.list_k_threshold = lo, hi, list_k_threshold
+        r.list = lst.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        r.list_k = lstk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        r.list_cap = cap
+        r.failures = fails.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        r.fail_cap = len(fails)
+        keep.append((lst, lstk, fails))
+    _check(lib.or_verify_ranges(arr, count, threads, margin, chunk), "verify_ranges")
+    out = [None] * count
+    for slot, i in enumerate(order):
+        r = arr[slot]
+        lo, hi = ranges[i]
+        if r.list_overflow or r.fail_len > r.fail_cap:
+            out[i] = verify_range(lo, hi, list_k_threshold, list_cap=int(r.list_len) + 1, threads=threads,
+                                  margin=margin, chunk=chunk)
+            continue
+        lst, lstk, fails = keep[slot]
+        ll = int(r.list_len)
+        out[i] = RangeResult(
+            lo=lo, hi=hi, n_odd=int(r.n_odd), hist=[int(x) for x in r.hist],
+            first_n=[int(x) for x in r.first_n], ksum=int(r.ksum), kmax=int(r.kmax),
+            list_n=lst[:ll].copy(), list_k=lstk[:ll].copy(), list_overflow=False,
+            failures=fails[:int(r.fail_len)].copy())
+    return out

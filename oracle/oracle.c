@@ -319,8 +319,17 @@ static int cmp_u64(const void *x, const void *y)
     return (a > b) - (a < b);
 }
 
+/*
+ * One range, Algorithm 1 + Algorithm 2 per chunk (or the definition, when
+ * use_sieve is 0).  table/table_np/table_cover: a prime list the caller built
+ * already (every odd prime <= table_cover, ascending), used when it covers
+ * isqrt(hi - 1); NULL builds the range's own list.  Primes beyond the range's
+ * own sqrt change nothing: Algorithm 1 stops at p^2 >= end and the trial
+ * division at p^2 > s.
+ */
 static int verify_range_impl(or_result *r, int nthreads, int use_sieve, uint64_t margin,
-                             uint64_t chunk)
+                             uint64_t chunk, const uint32_t *table, int64_t table_np,
+                             uint64_t table_cover)
 {
     if (!r || r->hi > ((uint64_t)1 << 62)) return OR_EINVAL;
     uint64_t lo = r->lo < 3 ? 3 : r->lo;
@@ -342,16 +351,26 @@ static int verify_range_impl(or_result *r, int nthreads, int use_sieve, uint64_t
     if (margin & 1) margin++;
 
     uint64_t pmax = or_isqrt(r->hi - 1);
-    int64_t np = or_odd_primes(pmax, NULL, 0);
-    if (np < 0) return (int)np;
-    uint32_t *primes = (uint32_t *)malloc((size_t)(np + 1) * sizeof(uint32_t));
-    if (!primes) return OR_ENOMEM;
-    or_odd_primes(pmax, primes, np);
+    int64_t np;
+    uint32_t *primes = NULL;      /* owned here when the range builds its own list */
+    const uint32_t *plist;
+    if (table && table_cover >= pmax) {
+        plist = table;
+        np = table_np;
+        pmax = table_cover;
+    } else {
+        np = or_odd_primes(pmax, NULL, 0);
+        if (np < 0) return (int)np;
+        primes = (uint32_t *)malloc((size_t)(np + 1) * sizeof(uint32_t));
+        if (!primes) return OR_ENOMEM;
+        or_odd_primes(pmax, primes, np);
+        plist = primes;
+    }
 
     shared_state sh;
     memset(&sh, 0, sizeof(sh));
     sh.job = r;
-    sh.primes = primes;
+    sh.primes = plist;
     sh.np = np;
     sh.cover = pmax;
     sh.nlo = nlo;
@@ -429,7 +448,7 @@ static int verify_range_impl(or_result *r, int nthreads, int use_sieve, uint64_t
     }
     free(ws);
     free(th);
-    free(primes);
+    free(primes); /* NULL when the caller's list was used */
     pthread_mutex_destroy(&sh.mu);
     if (err) return err;
     for (int k = 1; k < 64; k++) {
@@ -442,13 +461,89 @@ static int verify_range_impl(or_result *r, int nthreads, int use_sieve, uint64_t
 /* The paper's method: Algorithm 1 + Algorithm 2 per chunk, look-back margin W. */
 int or_verify_range(or_result *r, int nthreads, uint64_t margin, uint64_t chunk)
 {
-    return verify_range_impl(r, nthreads, 1, margin, chunk);
+    return verify_range_impl(r, nthreads, 1, margin, chunk, NULL, 0, 0);
 }
 
 /* The definition written out: every n - 2^k decided by trial division. */
 int or_verify_range_brute(or_result *r, int nthreads)
 {
-    return verify_range_impl(r, nthreads, 0, 0, (uint64_t)1 << 16);
+    return verify_range_impl(r, nthreads, 0, 0, (uint64_t)1 << 16, NULL, 0, 0);
+}
+
+/*
+ * Many independent ranges: the same computation as or_verify_range for each
+ * of rs[0 .. count), with one prime list (for the largest hi) shared by all,
+ * and the ranges handed out to nthreads workers, one whole range each, in
+ * the order given.
+ */
+typedef struct {
+    or_result *rs;
+    int64_t count;
+    int64_t next; /* guarded by mu */
+    pthread_mutex_t mu;
+    const uint32_t *primes;
+    int64_t np;
+    uint64_t cover, margin, chunk;
+    int err;
+} batch_state;
+
+static void *batch_worker(void *arg)
+{
+    batch_state *b = (batch_state *)arg;
+    for (;;) {
+        pthread_mutex_lock(&b->mu);
+        int64_t i = b->next++;
+        int stop = b->err != 0;
+        pthread_mutex_unlock(&b->mu);
+        if (stop || i >= b->count) break;
+        int e = verify_range_impl(&b->rs[i], 1, 1, b->margin, b->chunk, b->primes, b->np, b->cover);
+        if (e) {
+            pthread_mutex_lock(&b->mu);
+            if (!b->err) b->err = e;
+            pthread_mutex_unlock(&b->mu);
+        }
+    }
+    return NULL;
+}
+
+int or_verify_ranges(or_result *rs, int64_t count, int nthreads, uint64_t margin, uint64_t chunk)
+{
+    if (count < 0 || (count && !rs)) return OR_EINVAL;
+    uint64_t max_hi = 2;
+    for (int64_t i = 0; i < count; i++) {
+        if (rs[i].hi > ((uint64_t)1 << 62)) return OR_EINVAL;
+        if (rs[i].hi > max_hi) max_hi = rs[i].hi;
+    }
+    batch_state b;
+    memset(&b, 0, sizeof(b));
+    b.rs = rs;
+    b.count = count;
+    b.margin = margin;
+    b.chunk = chunk;
+    b.cover = or_isqrt(max_hi - 1);
+    b.np = or_odd_primes(b.cover, NULL, 0);
+    if (b.np < 0) return (int)b.np;
+    uint32_t *primes = (uint32_t *)malloc((size_t)(b.np + 1) * sizeof(uint32_t));
+    if (!primes) return OR_ENOMEM;
+    or_odd_primes(b.cover, primes, b.np);
+    b.primes = primes;
+    pthread_mutex_init(&b.mu, NULL);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    int started = 0;
+    if (!th) b.err = OR_ENOMEM;
+    for (int t = 0; t < nthreads && th; t++) {
+        if (pthread_create(&th[t], NULL, batch_worker, &b) != 0) {
+            if (!started) b.err = OR_ENOMEM;
+            break;
+        }
+        started++;
+    }
+    for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+    free(th);
+    free(primes);
+    pthread_mutex_destroy(&b.mu);
+    return b.err;
 }
 
 /*

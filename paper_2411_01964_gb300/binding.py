@@ -59,6 +59,7 @@ _SIGS = {
     "sv_set_config": (ctypes.c_int, [_CTX, P(sv_config)]),
     "sv_init_primes": (ctypes.c_int, [_CTX, u64]),
     "sv_prime_count": (ctypes.c_int, [_CTX, P(u64), P(u64)]),
+    "sv_prime_table_copy": (ctypes.c_int, [_CTX, P(u32), P(u64), P(u64), P(u64), u64, P(u64)]),
     "sv_verify_range": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
     "sv_verify_range_noalloc": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
     "sv_verify_batch": (ctypes.c_int, [_CTX, P(u64), P(u64), ctypes.c_size_t, P(sv_range_result)]),
@@ -155,6 +156,21 @@ def sv_prime_count(ctx) -> tuple[int, int]:
     n, m = u64(), u64()
     check(load().sv_prime_count(ctx, ctypes.byref(n), ctypes.byref(m)), "sv_prime_count")
     return n.value, m.value
+
+
+def sv_prime_table_copy(ctx) -> tuple:
+    """The resident prime table as numpy arrays (p, mu, inv, lim)."""
+    n, _ = sv_prime_count(ctx)
+    nd = u64()
+    check(load().sv_prime_table_copy(ctx, None, None, None, None, 0, ctypes.byref(nd)), "sv_prime_table_copy")
+    p = np.zeros(max(n, 1), dtype=np.uint32)
+    mu = np.zeros(max(n, 1), dtype=np.uint64)
+    inv = np.zeros(max(nd.value, 1), dtype=np.uint64)
+    lim = np.zeros(max(nd.value, 1), dtype=np.uint64)
+    check(load().sv_prime_table_copy(ctx, p.ctypes.data_as(P(u32)), mu.ctypes.data_as(P(u64)),
+                                     inv.ctypes.data_as(P(u64)), lim.ctypes.data_as(P(u64)), n, ctypes.byref(nd)),
+          "sv_prime_table_copy")
+    return p[:n], mu[:n], inv[:nd.value], lim[:nd.value]
 
 
 def sv_verify_range(ctx, lo: int, hi: int, out: sv_range_result) -> int:

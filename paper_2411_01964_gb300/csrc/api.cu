@@ -1004,6 +1004,22 @@ sv_status sv_prime_count(const sv_ctx *c, uint64_t *count, uint64_t *largest) {
   return SV_OK;
 }
 
+sv_status sv_prime_table_copy(sv_ctx *c, uint32_t *p, uint64_t *mu, uint64_t *inv, uint64_t *lim, uint64_t cap,
+                              uint64_t *n_div) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  SV_ON_DEVICE(c);
+  std::lock_guard<std::mutex> lk(c->mu);
+  const uint64_t n = std::min<uint64_t>(cap, c->n_primes), nd = std::min<uint64_t>(cap, c->n_div);
+  if (n_div) *n_div = c->n_div;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SV_ECUDA;
+  if (p && n && cudaMemcpy(p, c->d_p, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return SV_ECUDA;
+  if (mu && n && cudaMemcpy(mu, c->d_mu, 8 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return SV_ECUDA;
+  if (inv && nd && cudaMemcpy(inv, c->d_inv, 8 * nd, cudaMemcpyDeviceToHost) != cudaSuccess) return SV_ECUDA;
+  if (lim && nd && cudaMemcpy(lim, c->d_lim, 8 * nd, cudaMemcpyDeviceToHost) != cudaSuccess) return SV_ECUDA;
+  return SV_OK;
+}
+
 uint64_t sv_bitmap_words(uint64_t lo, uint64_t hi) {
   const uint64_t jlo = lo / 2, jhi = hi / 2;
   if (jhi <= jlo) return 0;

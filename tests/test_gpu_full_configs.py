@@ -1,16 +1,14 @@
-"""Full-size workloads in the benchmark's launch configuration, checked by
-sampling against the oracle and by properties that hold at any size.
+"""Full-size workloads, in the benchmark's launch configuration, compared with
+the oracle element by element.
 
 C2 = [2^40, 2^40 + 2^34) (2^33 odd n) and C3 = [2^50 - 2^36, 2^50) (2^35 odd
-n) are too large for the oracle to redo in a test, so:
-  * every odd n is accounted for (sum of the histogram = n_odd, no failures,
-    mink <= 13 below 2^50 as the Theorem of Sec. 4 states);
-  * the device-resident launch with a per-n output agrees with the
-    aggregate-only launch the benchmark times;
-  * sampled per-n values and contiguous sub-windows (start, middle, tail)
-    equal the oracle's, and every listed n and every first occurrence has the
-    exponent the oracle assigns to it by trial division;
-  * the histogram fractions sit where Table 2's heuristic puts them.
+n): the device-resident launch the benchmark times is compared, whole, with
+the oracle's Algorithm 1 + Algorithm 2 over the same range (histogram, first
+occurrences, sum and maximum of mink, the complete ascending list of n with
+mink >= 6 and their exponents, failures).  The same range with a per-n output
+must agree with it, and sampled per-n values and contiguous windows must equal
+the oracle's.  C4 = the 4096 ranges of seed 7 at their drawn lengths, as one
+batched graph launch, each range against the oracle.
 """
 import numpy as np
 import pytest
@@ -19,12 +17,19 @@ from paper_2411_01964_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-# Table 2 (Sec. 2): c_k - c_{k-1}, the heuristic probability that mink = k
-TABLE2 = {1: 8.1056e-1, 2: 1.6530e-1, 3: 2.1980e-2, 4: 2.0092e-3, 5: 1.3216e-4, 6: 6.5857e-6}
-
 
 def odd_index_to_n(lo, i):
     return (max(lo, 3) | 1) + 2 * i
+
+
+def assert_same(g, o):
+    assert g.n_odd == o.n_odd
+    assert g.hist == o.hist
+    assert g.first_n == o.first_n
+    assert g.ksum == o.ksum and g.kmax == o.kmax
+    assert g.list_len == len(o.list_n)
+    assert np.array_equal(g.list_n, o.list_n) and np.array_equal(g.list_k, o.list_k)
+    assert g.fail_len == len(o.failures) and np.array_equal(g.failures, o.failures)
 
 
 @pytest.mark.parametrize("name", ["C2", "C3"])
@@ -33,26 +38,23 @@ def test_full_config(gpu, orc, name):
     lo, hi = inputs.CONFIGS[name]
     n_odd = (hi - (lo | 1) + 1) // 2
 
-    # 1. aggregate-only launch (what the benchmark times)
+    # 1. the aggregate-only launch the benchmark times, whole, against the oracle
     gpu.launch_range(lo, hi)
     agg = gpu.fetch_range(list_cap=1 << 20)
-    assert sum(agg.hist) == n_odd and agg.fail_len == 0
-    assert agg.kmax <= 13
-    assert agg.list_len == sum(agg.hist[6:]) == len(agg.list_n)
-    for k, p in TABLE2.items():
-        mean = n_odd * p
-        assert abs(agg.hist[k] - mean) < 6 * mean ** 0.5 + 0.01 * mean, (k, agg.hist[k], mean)
+    o = orc.verify_range(lo, hi, list_cap=1 << 20)
+    assert not o.list_overflow
+    assert_same(agg, o)
+    assert sum(agg.hist) == n_odd and agg.fail_len == 0 and agg.kmax <= 13  # Theorem, Sec. 4
 
     # 2. the same range with a per-n output on the device
     per_n = torch.empty(n_odd, dtype=torch.uint8, device="cuda")
     gpu.launch_range(lo, hi, per_n)
     full = gpu.fetch_range(list_cap=1 << 20)
-    assert full.hist == agg.hist and full.first_n == agg.first_n
-    assert np.array_equal(full.list_n, agg.list_n)
+    assert_same(full, o)
     counts = np.zeros(256, dtype=np.int64)
     for c0 in range(0, n_odd, 1 << 30):
         counts += torch.bincount(per_n[c0:c0 + (1 << 30)].to(torch.int32), minlength=256).cpu().numpy()
-    assert list(counts[1:64]) == agg.hist[1:64] and counts[0] == 0 and counts[255] == 0
+    assert list(counts[1:64]) == o.hist[1:64] and counts[0] == 0 and counts[255] == 0
 
     # 3. sampled points against the definition (trial division)
     idx = np.array(inputs.random_points(17, 600, 0, 2 * n_odd), dtype=np.int64) // 2
@@ -60,18 +62,30 @@ def test_full_config(gpu, orc, name):
     pts = [odd_index_to_n(lo, int(i)) for i in idx]
     assert np.array_equal(got, orc.min_k(pts))
 
-    # 4. contiguous windows against the oracle's range verification
+    # 4. contiguous windows of the per-n output against the oracle's
     for start in (0, n_odd // 2 + 12345, n_odd - (1 << 18)):
         a = odd_index_to_n(lo, start)
         b = a + 2 * (1 << 18)
-        o = orc.verify_range(a, b, per_n=True)
-        assert np.array_equal(per_n[start:start + (1 << 18)].cpu().numpy(), o.per_n_k)
+        w = orc.verify_range(a, b, per_n=True)
+        assert np.array_equal(per_n[start:start + (1 << 18)].cpu().numpy(), w.per_n_k)
 
-    # 5. listed n and first occurrences carry the oracle's exponent
-    sample = agg.list_n[:: max(1, len(agg.list_n) // 48)][:48]
-    ks = agg.list_k[:: max(1, len(agg.list_n) // 48)][:48]
-    assert np.array_equal(orc.min_k(sample), ks)
-    firsts = [(k, agg.first_n[k]) for k in range(1, 14) if agg.first_n[k] != (1 << 64) - 1]
-    assert list(orc.min_k([n for _, n in firsts])) == [k for k, _ in firsts]
-    del per_n
+    # 5. every listed n sits at its index of the per-n output with its mink
+    li = torch.tensor(((o.list_n.astype(np.int64) - (lo | 1)) // 2), device="cuda")
+    assert np.array_equal(per_n[li].cpu().numpy(), o.list_k)
+    del per_n, li
     torch.cuda.empty_cache()
+
+
+def test_full_batch_C4(orc):
+    """All 4096 ranges of seed 7 at their drawn lengths (starts odd in
+    [2^30, 2^50), lengths 2^10..2^28), as the benchmark launches them."""
+    from paper_2411_01964_gb300 import Verifier
+    reqs = inputs.batch_requests(7, 4096)
+    with Verifier(max_hi=inputs.TABLE_MAX_HI) as v:
+        v.launch_batch([a for a, _ in reqs], [b for _, b in reqs])
+        res = v.fetch_batch(list_cap=4096, fail_cap=16)
+    want = orc.verify_ranges(reqs)
+    assert sum(r.n_odd for r in res) == sum(o.n_odd for o in want)
+    for (lo, hi), g, o in zip(reqs, res, want):
+        assert g.lo == lo and g.hi == hi
+        assert_same(g, o)

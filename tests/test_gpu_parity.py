@@ -37,9 +37,22 @@ def assert_same_range(g, o, per_n=True):
 
 
 def test_prime_table(gpu, orc):
+    # element by element against the oracle's Eratosthenes, and every
+    # constant against its definition (numpy uint64 arithmetic is exact)
+    from paper_2411_01964_gb300 import B
     n, largest = gpu.prime_count()
     want = orc.odd_primes(orc.isqrt(inputs.TABLE_MAX_HI - 1))
     assert n == len(want) and largest == int(want[-1])
+    p, mu, inv, lim = B.sv_prime_table_copy(gpu.ctx)
+    assert np.array_equal(p, want)
+    p64 = p.astype(np.uint64)
+    top = np.uint64(2 ** 64 - 1)
+    assert np.array_equal(mu, top // (p64 * p64))                 # Barrett constant of p^2
+    nd = len(inv)
+    assert nd == int(np.searchsorted(p, 1 << 21))                 # every p < 2^21
+    with np.errstate(over="ignore"):
+        assert np.all(p64[:nd] * inv == np.uint64(1))             # p * p^-1 = 1 mod 2^64
+    assert np.array_equal(lim, top // p64[:nd])
 
 
 @pytest.mark.parametrize("lo,hi", [

@@ -218,3 +218,19 @@ def test_heuristic_fractions_plausible(orc):
     for k, p in probs.items():
         mean, sd = N * p, (N * p * (1 - p)) ** 0.5
         assert abs(r.hist[k] - mean) < 6 * sd + 0.002 * mean, (k, r.hist[k], mean)
+
+
+def test_batch_driver_equals_single_ranges(orc):
+    # the batch driver (one prime list for all ranges, whole ranges per
+    # worker) only reorganises the work: each range's result is the one the
+    # pinned single-range route gives
+    reqs = [(3, 1 << 20), (1 << 40, (1 << 40) + (1 << 20) + 2), ((1 << 50) - (1 << 18) - 3, (1 << 50) + 7),
+            (12345, 12345), (9, 10), (3, 4)] + inputs.batch_requests(7, 6)
+    reqs = [(lo, min(hi, lo + (1 << 20))) for lo, hi in reqs]
+    got = orc.verify_ranges(reqs)
+    for (lo, hi), g in zip(reqs, got):
+        o = orc.verify_range(lo, hi)
+        assert (g.lo, g.hi, g.n_odd, g.ksum, g.kmax) == (lo, hi, o.n_odd, o.ksum, o.kmax)
+        assert g.hist == o.hist and g.first_n == o.first_n
+        assert np.array_equal(g.list_n, o.list_n) and np.array_equal(g.list_k, o.list_k)
+        assert np.array_equal(g.failures, o.failures)
