@@ -77,6 +77,27 @@ def alu_ops_per_odd_n(hi: int) -> float:
     return per_word / 32.0
 
 
+def strikes_per_launch(lo: int, hi: int, cfg) -> float:
+    """Shared-memory atomics of one tile-kernel launch (algorithmic): every
+    window of 32 (tw + mw) bits takes window_bits / p^2 strikes of each prime
+    p >= 13 up to isqrt(hi - 1) (the stamped primes 3..11 are patterns, not
+    atomics)."""
+    import numpy as np
+    lim = math.isqrt(hi - 1)
+    sieve = np.ones(lim + 1, dtype=bool)
+    sieve[:2] = False
+    for i in range(2, math.isqrt(lim) + 1):
+        if sieve[i]:
+            sieve[i * i::i] = False
+    ps = np.nonzero(sieve)[0]
+    ps = ps[ps >= 13].astype(np.float64)
+    tw, mw = 1 << (cfg.tile_log2 - 5), 1 << (cfg.margin_log2 - 6)
+    jlo, jhi = (max(lo, 3) | 1) // 2, hi // 2
+    words = (jhi + 31) // 32 - jlo // 32
+    tiles = -(-words // tw)
+    return float(tiles * 32 * (tw + mw) * np.sum(1.0 / (ps * ps)))
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -422,6 +443,7 @@ def main() -> int:
     v.fetch_range()
     assert sum(res.hist) + res.fail_len == n_odd
 
+    pk = B.sv_measure_peaks(v.ctx)  # after the timed region: the probes run on the same stream
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -447,13 +469,15 @@ def main() -> int:
     e2e_value = n_odd * world * e2e_steps / e2e_s if e2e_steps else None
     assert rr.hist == res.hist
 
-    peaks = measured_peaks()
+    drv = measured_peaks()
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = props.multi_processor_count * 128 * sm_max * 1e6  # int32 lane-ops/s
     ops_per_n = alu_ops_per_odd_n(hi)
     tile_avg_s = (tile_ms / max(tile_n, 1)) / 1e3
     achieved = ops_per_n * n_odd / tile_avg_s
+    strikes = strikes_per_launch(lo, hi, v.config)
+    atom_rate = strikes / tile_avg_s
+    alu_peak = pk["scan_mix_ops_per_s"]
+    nominal = props.multi_processor_count * 128 * float(drv.get("sm_max_mhz", 2070.0)) * 1e6
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -469,9 +493,17 @@ def main() -> int:
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "int32 ops/s",
                      "frac": achieved / alu_peak, "traffic": measured_traffic(n_odd),
                      "kernel": "tile_kernel (sieve + scan, fused)",
+                     "peak_source": "measured in this run: sv_measure_peaks, the scan's integer mix "
+                                    "(funnel shift, AND-NOT, popcount, add) on every SM",
                      "ops_per_odd_n": ops_per_n, "kernel_avg_ms": tile_avg_s * 1e3,
                      "kernel_share": tile_ms / total_ms if total_ms else None,
-                     "peak_basis": f"{props.multi_processor_count} SMs x 128 INT32 lanes x {sm_max:.0f} MHz"},
+                     "frac_of_nominal_int32": achieved / nominal,
+                     "smem_atomics_per_launch": strikes, "smem_atomics_per_s": atom_rate,
+                     "smem_atomic_peak": pk["smem_atomic_strike_per_s"],
+                     "smem_atomic_frac": atom_rate / pk["smem_atomic_strike_per_s"],
+                     "smem_atomic_peak_source": "measured in this run: sv_measure_peaks, atomicAnd in the "
+                                                "dense-strike pattern on every SM"},
+        "peaks": {**pk, "hbm_gbs": drv.get("hbm_gbs"), "hbm_source": "MEASURED_PEAKS.json (copy bandwidth)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(e2e_steps, 1),
                 "d2h_bytes_per_step": d2h // max(e2e_steps, 1)},
         "gpu_launches": launches,

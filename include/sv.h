@@ -321,6 +321,31 @@ sv_status sv_last_transfer(const sv_ctx *ctx, uint64_t *h2d_bytes, uint64_t *d2h
  */
 sv_status sv_verify_range_noalloc(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_range_result *out);
 
+/*
+ * Measured peaks of this GPU for the rooflines of the tile kernel (Algorithms 1
+ * and 2 of Sec. 3 fused): the strikes of Algorithm 1 are shared-memory atomics
+ * and the word-parallel Algorithm 2 is integer work.  Rates are for the whole
+ * GPU (every SM at full occupancy), per second.
+ */
+typedef struct sv_peaks {
+    double smem_atomic_per_s;        /* 32-bit shared-memory atomicAnd, the 32 lanes of a warp on 32 banks */
+    double smem_atomic_strike_per_s; /* the same in the dense-strike pattern: lanes q = p^2 bits apart */
+    double scan_mix_ops_per_s;       /* funnel shift, AND-NOT, popcount, add (one scan step = 4 ops) */
+    double int_alu_ops_per_s;        /* three-input logic and 32-bit add */
+    double popc_per_s;               /* population counts, in a loop of one popcount per four operations */
+    double sm_clock_max_mhz;         /* the device's maximum SM clock (attribute, not measured) */
+    uint32_t sms;                    /* streaming multiprocessors */
+    uint32_t reserved;
+} sv_peaks;
+
+/*
+ * Runs the microbenchmarks behind sv_peaks on the context's device: each probe
+ * kernel runs a few milliseconds on every SM, timed with CUDA events on the
+ * context's stream (best of five after a warm-up).  Allocates a small scratch
+ * buffer; changes no device setting.  Errors: SV_EINVAL, SV_ENOMEM, SV_ECUDA.
+ */
+sv_status sv_measure_peaks(sv_ctx *ctx, sv_peaks *out);
+
 /* Number of kernels this context has launched so far. */
 uint64_t sv_kernel_launches(const sv_ctx *ctx);
 

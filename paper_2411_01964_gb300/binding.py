@@ -50,6 +50,13 @@ class sv_server_stats(ctypes.Structure):
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double)]
 
 
+class sv_peaks(ctypes.Structure):
+    _fields_ = [("smem_atomic_per_s", ctypes.c_double), ("smem_atomic_strike_per_s", ctypes.c_double),
+                ("scan_mix_ops_per_s", ctypes.c_double), ("int_alu_ops_per_s", ctypes.c_double),
+                ("popc_per_s", ctypes.c_double), ("sm_clock_max_mhz", ctypes.c_double), ("sms", u32),
+                ("reserved", u32)]
+
+
 _CTX = ctypes.c_void_p
 _SIGS = {
     "sv_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -79,6 +86,7 @@ _SIGS = {
     "sv_server_stats_get": (ctypes.c_int, [_CTX, P(sv_server_stats)]),
     "sv_last_transfer": (ctypes.c_int, [_CTX, P(u64), P(u64)]),
     "sv_kernel_launches": (u64, [_CTX]),
+    "sv_measure_peaks": (ctypes.c_int, [_CTX, P(sv_peaks)]),
     "sv_kernel_timing": (ctypes.c_int, [_CTX, ctypes.c_int]),
     "sv_kernel_time": (ctypes.c_int, [_CTX, ctypes.c_int, P(ctypes.c_double), P(u64)]),
 }
@@ -281,3 +289,10 @@ def sv_kernel_time(ctx, kernel: int) -> tuple[float, int]:
     ms, n = ctypes.c_double(), u64()
     check(load().sv_kernel_time(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)), "sv_kernel_time")
     return ms.value, n.value
+
+
+def sv_measure_peaks(ctx) -> dict:
+    """Measured shared-memory atomic and integer peaks of the context's GPU."""
+    pk = sv_peaks()
+    check(load().sv_measure_peaks(ctx, ctypes.byref(pk)), "sv_measure_peaks")
+    return {name: getattr(pk, name) for name, _ in sv_peaks._fields_ if name != "reserved"}
