@@ -224,6 +224,54 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3) -> dict:
             "speedup_vs_plain": pt / ms, "graph": "one captured graph, replayed per batch"}
 
 
+def bench_plain(v, stream, flush, lo: int, hi: int, steps: int, fused: dict, hbm_gbs: float | None) -> dict:
+    """The plain (unfused) path on the same range: Algorithm 1 writes the
+    bitmap to device memory, Algorithm 2 reads it back.  Device time per step
+    (CUDA events on the stream), each pass's tile kernel timed by its own
+    events, and the HBM bandwidth each pass reaches on the bitmap."""
+    import torch
+    from paper_2411_01964_gb300 import binding as B
+    for _ in range(2):
+        v.launch_range_plain(lo, hi)
+        r = v.fetch_range(list_cap=1 << 20)
+    same = (r.hist == fused["hist"] and r.first_n == fused["first_n"] and r.list_len == fused["list_len"]
+            and bool((r.list_n == fused["list_n"]).all()))
+    B.sv_kernel_timing(v.ctx, ["sieve_pass", "scan_pass"])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        v.launch_range_plain(lo, hi)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    s_ms, s_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["sieve_pass"])
+    c_ms, c_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["scan_pass"])
+    B.sv_kernel_timing(v.ctx, False)
+    v.fetch_range(list_cap=16)
+    s_ms /= max(s_n, 1)
+    c_ms /= max(c_n, 1)
+    cfg = v.config
+    tw, mw = 1 << (cfg.tile_log2 - 5), 1 << (cfg.margin_log2 - 6)
+    jlo, jhi = (max(lo, 3) | 1) // 2, hi // 2
+    words = (jhi + 31) // 32 - jlo // 32
+    bitmap = 4 * (words + mw)                     # one bit per odd integer, margin included
+    tiles = -(-words // tw)
+    scan_read = 4 * tiles * (tw + mw)             # every window, margin re-read
+    n_odd = odd_count(lo, hi)
+    w_gbs, r_gbs = bitmap / (s_ms * 1e6), scan_read / (c_ms * 1e6)
+    return {"workload": "the same range, bitmap through device memory (sieve pass, then scan pass)",
+            "ms_per_step": ms, "value": n_odd / (ms / 1e3), "unit": UNIT,
+            "equal_to_fused": same, "vs_fused": fused["ms"] / ms,
+            "sieve_pass_ms": s_ms, "scan_pass_ms": c_ms, "bitmap_bytes": bitmap,
+            "roofline_hbm": {"bound": "hbm", "unit": "GB/s", "peak": hbm_gbs,
+                             "peak_source": "MEASURED_PEAKS.json copy bandwidth",
+                             "sieve_pass": {"achieved": w_gbs, "traffic_algorithmic": bitmap,
+                                            "frac": w_gbs / hbm_gbs if hbm_gbs else None},
+                             "scan_pass": {"achieved": r_gbs, "traffic_algorithmic": scan_read,
+                                           "frac": r_gbs / hbm_gbs if hbm_gbs else None}}}
+
+
 def bench_serving(stream, seconds: float, batched: dict | None) -> dict:
     """Config 5: Poisson arrivals (seed 11) of the serving mix at several
     rates; latency from submission to completion, throughput over the run."""
@@ -360,6 +408,7 @@ def main() -> int:
     ap.add_argument("--range", default="", help="LO:HI overrides the workload's range (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=4096)
     ap.add_argument("--serve-seconds", type=float, default=1.5)
@@ -430,7 +479,7 @@ def main() -> int:
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     tile_ms, tile_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["tile"])
-    res = v.fetch_range()
+    res = v.fetch_range(list_cap=1 << 20)
     # the other kernels' times, from a few more steps outside the timed region
     B.sv_kernel_timing(v.ctx, True)
     for _ in range(min(args.steps, 10)):
@@ -517,6 +566,10 @@ def main() -> int:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], o = cpu_baseline(lo, hi, args.cpu_seconds, hi - lo)
         line["parity"] = parity_check(v, o)
+    if rank == 0 and world == 1 and not args.no_plain:
+        fused = {"hist": res.hist, "first_n": res.first_n, "list_len": res.list_len, "list_n": res.list_n,
+                 "ms": total_ms / args.steps}
+        line["plain_hbm"] = bench_plain(v, stream, flush, lo, hi, min(args.steps, 20), fused, drv.get("hbm_gbs"))
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched"] = bench_batch(v, stream, flush, args.batch_requests)
     if rank == 0 and world == 1 and not args.no_serve:

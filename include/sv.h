@@ -13,8 +13,9 @@
  * Conventions shared by every entry point
  *   - All arithmetic is exact unsigned 64-bit integer arithmetic: the device
  *     code uses no floating point at all (square roots are integer Newton
- *     iterations), and the host uses it only to estimate buffer sizes, which
- *     never changes a result.
+ *     iterations).  The host uses floating point only for estimates that never
+ *     change a result: buffer sizes, and the first guess of an integer square
+ *     root that exact integer steps then correct.
  *   - Every entry point makes the context's CUDA device current while it runs
  *     and gives the calling thread its own current device back afterwards.
  *   - squarefree(s): s >= 1 and no prime p with p^2 | s.  1 is squarefree.
@@ -214,6 +215,26 @@ sv_status sv_sieve_bitmap(sv_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t *d_bit
 uint64_t sv_bitmap_words(uint64_t lo, uint64_t hi);
 
 /*
+ * The plain (unfused) form of sv_verify_range, with the bitmap through device
+ * memory as Sec. 3 describes it: Algorithm 1 writes the squarefree flags of
+ * the odd integers from the range's look-back margin up to hi into a bitmap in
+ * device memory (one bit per odd integer, 128-bit bulk stores from shared
+ * memory), then Algorithm 2 reads them back tile by tile (bulk loads into
+ * shared memory) and finds mink.  Results are identical to sv_verify_range;
+ * the fused path is faster because its bitmap never leaves shared memory.
+ * The bitmap (about (hi - lo) / 16 bytes) is owned by the context and kept
+ * for the next call.  out as for sv_verify_range (HOST buffers).  Blocking.
+ * Errors: as sv_verify_range, and SV_ETIMEDOUT if a bulk copy did not
+ * complete within about a second.
+ */
+sv_status sv_verify_range_plain(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_range_result *out);
+
+/* Device-resident form of sv_verify_range_plain: both passes are enqueued on
+ * the context's stream without waiting; sv_fetch_range collects the result.
+ * d_per_n_k as for sv_launch_range. */
+sv_status sv_launch_range_plain(sv_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *d_per_n_k);
+
+/*
  * Device-resident form of sv_verify_range: enqueue the whole range on the
  * context's stream and return without waiting; results stay in device memory
  * until sv_fetch_range.  d_per_n_k is an optional caller-owned DEVICE buffer
@@ -221,7 +242,7 @@ uint64_t sv_bitmap_words(uint64_t lo, uint64_t hi);
  */
 sv_status sv_launch_range(sv_ctx *ctx, uint64_t lo, uint64_t hi, uint8_t *d_per_n_k);
 
-/* Wait for the pending sv_launch_range and copy its aggregates to *out
+/* Wait for the pending sv_launch_range (or sv_launch_range_plain) and copy its aggregates to *out
  * (out->per_n_k is ignored: the per-n values are already in the device
  * buffer given to sv_launch_range). */
 sv_status sv_fetch_range(sv_ctx *ctx, sv_range_result *out);
@@ -354,7 +375,8 @@ uint64_t sv_kernel_launches(const sv_ctx *ctx);
  * replayed from a captured graph are not timed).  enable: 0 off, -1 every
  * kernel, otherwise a bit mask of kernel ids (bit i: id i); every call resets
  * the totals.  Kernel ids: 0 init, 1 bucket fill, 2 tile (sieve + scan),
- * 3 stragglers, 4 points, 5 ordered-list compaction. */
+ * 3 stragglers, 4 points, 5 ordered-list compaction, 6 tile kernel of the
+ * plain path's sieve pass, 7 tile kernel of the plain path's scan pass. */
 sv_status sv_kernel_timing(sv_ctx *ctx, int enable);
 
 /* Total milliseconds and launch count of one kernel id since the last reset

@@ -140,6 +140,13 @@ class Verifier:
         B.check(B.sv_verify_range(self.ctx, lo, hi, buf.res), "sv_verify_range")
         return buf.result()
 
+    def verify_range_plain(self, lo: int, hi: int, *, list_cap: int = 1 << 16, fail_cap: int = 1024,
+                           per_n: bool = False) -> RangeResult:
+        """The plain (unfused) path: the bitmap through device memory."""
+        buf = _ResultBuffers(list_cap, fail_cap, odd_count(lo, hi) if per_n else None)
+        B.check(B.sv_verify_range_plain(self.ctx, lo, hi, buf.res), "sv_verify_range_plain")
+        return buf.result()
+
     def verify_batch(self, los, his, *, list_cap: int = 1 << 12, fail_cap: int = 64) -> list:
         n = len(los)
         bufs = [_ResultBuffers(list_cap, fail_cap, None) for _ in range(n)]
@@ -172,6 +179,10 @@ class Verifier:
     def launch_range(self, lo: int, hi: int, d_per_n=None) -> None:
         ptr = d_per_n.data_ptr() if d_per_n is not None else None
         B.check(B.sv_launch_range(self.ctx, lo, hi, ptr), "sv_launch_range")
+
+    def launch_range_plain(self, lo: int, hi: int, d_per_n=None) -> None:
+        ptr = d_per_n.data_ptr() if d_per_n is not None else None
+        B.check(B.sv_launch_range_plain(self.ctx, lo, hi, ptr), "sv_launch_range_plain")
 
     def fetch_range(self, *, list_cap: int = 1 << 16, fail_cap: int = 1024) -> RangeResult:
         buf = _ResultBuffers(list_cap, fail_cap, None)

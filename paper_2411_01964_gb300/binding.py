@@ -77,6 +77,8 @@ _SIGS = {
     "sv_sieve_bitmap": (ctypes.c_int, [_CTX, u64, u64, ctypes.c_void_p]),
     "sv_bitmap_words": (u64, [u64, u64]),
     "sv_launch_range": (ctypes.c_int, [_CTX, u64, u64, ctypes.c_void_p]),
+    "sv_verify_range_plain": (ctypes.c_int, [_CTX, u64, u64, P(sv_range_result)]),
+    "sv_launch_range_plain": (ctypes.c_int, [_CTX, u64, u64, ctypes.c_void_p]),
     "sv_fetch_range": (ctypes.c_int, [_CTX, P(sv_range_result)]),
     "sv_synchronize": (ctypes.c_int, [_CTX]),
     "sv_autotune": (ctypes.c_int, [_CTX, u64, u64, P(sv_config)]),
@@ -225,6 +227,14 @@ def sv_launch_range(ctx, lo: int, hi: int, d_per_n_ptr: int | None = None) -> in
     return load().sv_launch_range(ctx, lo, hi, d_per_n_ptr)
 
 
+def sv_verify_range_plain(ctx, lo: int, hi: int, out: sv_range_result) -> int:
+    return load().sv_verify_range_plain(ctx, lo, hi, ctypes.byref(out))
+
+
+def sv_launch_range_plain(ctx, lo: int, hi: int, d_per_n_ptr: int | None = None) -> int:
+    return load().sv_launch_range_plain(ctx, lo, hi, d_per_n_ptr)
+
+
 def sv_fetch_range(ctx, out: sv_range_result) -> int:
     return load().sv_fetch_range(ctx, ctypes.byref(out))
 
@@ -269,7 +279,8 @@ def sv_kernel_launches(ctx) -> int:
     return int(load().sv_kernel_launches(ctx))
 
 
-KERNEL_IDS = {"init": 0, "bucket_fill": 1, "tile": 2, "stragglers": 3, "points": 4, "list_compact": 5}
+KERNEL_IDS = {"init": 0, "bucket_fill": 1, "tile": 2, "stragglers": 3, "points": 4, "list_compact": 5,
+              "sieve_pass": 6, "scan_pass": 7}
 
 
 def sv_kernel_timing(ctx, enable) -> None:

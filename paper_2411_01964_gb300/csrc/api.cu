@@ -38,6 +38,9 @@ void Workspace::release_all() {
   bucket_count.release();
   bucket_data.release();
   per_n.release();
+  stage_n.release();
+  stage_k.release();
+  stage_cnt.release();
   points.release();
   points_out.release();
   h_points.release();
@@ -45,24 +48,14 @@ void Workspace::release_all() {
 }
 
 uint64_t host_isqrt(uint64_t x) {
-  // floor(sqrt(x)) by Newton's iteration from above, integer only: the start
-  // 2^ceil(bits/2) is at least the root, and the iterates fall to it
-  if (x < 2) return x;
-  const int bits = 64 - __builtin_clzll(x);
-  uint64_t r = 1ull << ((bits + 1) / 2);
-  for (;;) {
-    const uint64_t y = (r + x / r) / 2;
-    if (y >= r) return r;
-    r = y;
-  }
-}
-
-// The square roots of the bucket fill's odd-multiple interval ends (ReqDesc).
-void set_interval_roots(ReqDesc &d, uint32_t mw) {
-  const int64_t ws = d.w0 - (int64_t)mw;
-  const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
-  d.sq_lo = (uint32_t)host_isqrt(2 * A);
-  d.sq_hi = d.jhi ? (uint32_t)host_isqrt(2 * d.jhi - 1) : 0u;
+  // floor(sqrt(x)): a double-precision first guess (within a few units of
+  // the root), then exact integer steps to r^2 <= x < (r+1)^2 (r < 2^32, so
+  // the squares do not overflow)
+  uint64_t r = (uint64_t)std::sqrt((double)x);
+  if (r > 0xFFFFFFFFull) r = 0xFFFFFFFFull;
+  while (r > 0 && r * r > x) --r;
+  while (r < 0xFFFFFFFFull && (r + 1) * (r + 1) <= x) ++r;
+  return r;
 }
 
 uint64_t range_odd_count(uint64_t lo, uint64_t hi) {
@@ -217,6 +210,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   uint64_t j_max = 0;
   const uint64_t ph2 = g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb;
   bool any_per_n = false;
+  bool all_from_bitmap = n > 0;
   for (uint32_t r = 0; r < n; ++r) {
     const RangeSpec &s = specs[r];
     ReqDesc d{};
@@ -252,8 +246,10 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
     d.fail_cap = s.fail_cap;
     fail_total += s.fail_cap;
     d.sieve_only = s.sieve_only ? 1u : 0u;
-    set_interval_roots(d, g.mw);
     d.bitmap_out = s.bitmap_out;
+    d.bitmap_in = s.bitmap_in;
+    d.bitmap_w0 = s.bitmap_w0;
+    all_from_bitmap &= (s.bitmap_in != nullptr);
     ws.h_reqs.p[r] = d;
   }
   LaunchHeader h{};
@@ -268,6 +264,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   ws.fail_total = fail_total;
   ws.j_max = j_max;
   ws.any_per_n = any_per_n;
+  ws.all_from_bitmap = all_from_bitmap;
   ws.ordered = !any_per_n && g.rec_t > 5 && !ws.force_general;
   return SV_OK;
 }
@@ -286,7 +283,8 @@ bool ensure_stage(Workspace &ws) {
 uint32_t fill_blocks(const sv_ctx *c) { return (uint32_t)c->num_sms * kFillBlocksPerSm; }
 
 // Kernel ids of the per-kernel timing.
-enum { kKInit = 0, kKBucket = 1, kKTiles = 2, kKStrag = 3, kKPoints = 4, kKCompact = 5 };
+enum { kKInit = 0, kKBucket = 1, kKTiles = 2, kKStrag = 3, kKPoints = 4, kKCompact = 5, kKSievePass = 6,
+       kKScanPass = 7 };
 
 cudaEvent_t pool_event(sv_ctx *c) {
   if (!c->ev_pool.empty()) {
@@ -340,12 +338,12 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
   {
     KTimer kt(c, kKInit, st);
     SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, mode == 0 ? ws.stage_cnt.p : nullptr,
-                            ws.total_tiles, st));
+                            ws.total_tiles, ws.reqs.p, g.mw, st));
     kt.done();
   }
   c->launches++;
   const PrimeTab pt = prime_tab(c);
-  if (ws.max_primes > g.i_large && ws.total_tiles) {
+  if (ws.max_primes > g.i_large && ws.total_tiles && !ws.all_from_bitmap) {
     BucketArgs b{};
     b.pt = pt;
     b.g = g;
@@ -381,7 +379,7 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
     uint32_t grid = (uint32_t)c->num_sms * c->cfg.ctas_per_sm;
     if (grid > ws.total_tiles) grid = ws.total_tiles;
     {
-      KTimer kt(c, kKTiles, st);
+      KTimer kt(c, ws.tile_kernel_id, st);
       SV_TRY_CUDA(launch_tiles(t, c->cfg.threads, grid, smem, mode, st));
       kt.done();
     }
@@ -470,7 +468,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
     // sized for the buffers (the kernel reads the launch's sizes from the header)
     if (!e) e = launch_init(ws.hdr.p, ws.slots.p, (uint32_t)std::min<size_t>(ws.slots.cap, 1u << 20), ws.bucket_count.p,
                             mode == 0 ? ws.stage_cnt.p : nullptr, (uint32_t)std::min<size_t>(ws.bucket_count.cap, 1u << 30),
-                            st);
+                            ws.reqs.p, g.mw, st);
     if (!e && pt.n > g.i_large) {
       BucketArgs b{};
       b.pt = pt;
@@ -621,6 +619,7 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
   uint64_t d2h = sizeof(LaunchHeader) + sizeof(ResultSlot) * n + 9 * spec_end;
   const uint32_t status = ws.h_hdr.p->status;
   if (status & kStBadTile) return SV_ECUDA;
+  if (status & kStTimeout) return SV_ETIMEDOUT;
   if (status & kStBucketOverflow) {
     *what = kRetryBucket;
     return SV_OK;
@@ -793,6 +792,117 @@ sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result *
   return SV_EOVERFLOW;
 }
 
+// ---- the plain (unfused) path -------------------------------------------------
+// Algorithm 1 writes the squarefree flags of the odd integers to a bitmap in
+// device memory (the sieve pass: sieve_only tiles, one bulk store per tile),
+// and Algorithm 2 reads them back (the scan pass: every tile's window comes
+// from the bitmap by one bulk load).  The bitmap starts at the first window's
+// start, max(w0 - mw, 0) words, so every window of the scan lies inside it.
+
+// The two passes' ranges for [lo, hi); an empty range has no sieve pass.
+sv_status plain_specs(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n, uint64_t list_cap, uint64_t fail_cap,
+                      std::vector<RangeSpec> &sieve, std::vector<RangeSpec> &scan) {
+  const int64_t mw = (int64_t)1 << (c->cfg.margin_log2 - 6);
+  const uint64_t nlo = (lo < 3 ? 3 : lo) | 1ull, jlo = (nlo - 1) / 2;
+  const uint64_t jhi = std::max<uint64_t>(hi / 2, jlo);
+  scan.assign(1, RangeSpec{});
+  scan[0].lo = lo;
+  scan[0].hi = hi;
+  scan[0].d_per_n = d_per_n;
+  scan[0].list_cap = list_cap;
+  scan[0].fail_cap = fail_cap;
+  sieve.clear();
+  if (jhi <= jlo) return SV_OK;
+  const int64_t bw0 = std::max<int64_t>((int64_t)(jlo >> 5) - mw, 0);
+  const uint64_t words = ((jhi + 31) >> 5) - (uint64_t)bw0;
+  if (c->plain_bitmap.ensure(words + 4)) return SV_ENOMEM;  // room for a bulk load rounded up to 16 bytes
+  RangeSpec sp;
+  sp.lo = 64ull * (uint64_t)bw0;
+  sp.hi = hi;
+  sp.sieve_only = true;
+  sp.bitmap_out = c->plain_bitmap.p;
+  sieve.push_back(sp);
+  scan[0].bitmap_in = c->plain_bitmap.p;
+  scan[0].bitmap_w0 = bw0;
+  return SV_OK;
+}
+
+// Enqueues the sieve pass (its own workspace) and the scan pass on st.
+sv_status plain_enqueue(sv_ctx *c, std::vector<RangeSpec> &sieve, std::vector<RangeSpec> &scan, cudaStream_t st) {
+  sv_status s = ensure_tile_smem(c);
+  if (s) return s;
+  Geometry g = make_geometry(c, max_span_bits(c, sieve.empty() ? scan : sieve));
+  if (c->ws_sieve.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws_sieve.bucket_cap;
+  if (!sieve.empty()) {
+    c->ws_sieve.force_general = true;  // no lists in the sieve pass: no staging, no compaction
+    c->ws_sieve.tile_kernel_id = kKSievePass;
+    if ((s = plan(c, sieve, g, c->ws_sieve))) return s;
+    if ((s = enqueue(c, g, c->ws_sieve, st))) return s;
+  }
+  c->ws.tile_kernel_id = sieve.empty() ? kKTiles : kKScanPass;
+  if ((s = plan(c, scan, g, c->ws))) return s;
+  s = enqueue(c, g, c->ws, st);
+  c->ws.tile_kernel_id = kKTiles;
+  return s;
+}
+
+// Waits for both passes and collects the scan's results into *out.  A retry
+// the sieve pass needs is reported through *what with *sieve_retry set.
+sv_status plain_collect(sv_ctx *c, const std::vector<RangeSpec> &sieve, const std::vector<RangeSpec> &scan,
+                        sv_range_result *out, cudaStream_t st, Collect *what, bool *sieve_retry) {
+  *sieve_retry = false;
+  if (!sieve.empty()) {
+    Collect w1;
+    sv_status s = collect(c, sieve, nullptr, c->ws_sieve, st, &w1);
+    if (s) return s;
+    if (w1 != kDone) {
+      *what = w1;
+      *sieve_retry = true;
+      return SV_OK;
+    }
+  }
+  sv_range_result *outs[1] = {out};
+  return collect(c, scan, outs, c->ws, st, what);
+}
+
+// Adjusts the buffers after an overflow either pass reported.
+void plain_retry(sv_ctx *c, Collect what, bool sieve_retry, std::vector<RangeSpec> &sieve, std::vector<RangeSpec> &scan,
+                 const sv_range_result *out) {
+  if (sieve_retry) {
+    if (what == kRetryBucket)
+      c->ws_sieve.bucket_cap =
+          std::max<uint32_t>(c->ws_sieve.bucket_cap, make_geometry(c, max_span_bits(c, sieve)).bucket_auto) * 4;
+    return;
+  }
+  if (what == kRetryStrag) c->ws.strag_cap *= 4;
+  if (what == kRetryGeneral) c->ws.force_general = true;
+  if (what == kRetryList) {
+    uint64_t cap = std::min<uint64_t>(c->ws.h_slots.p[0].list_count, kListRetryMax);
+    if (c->ws.ordered) cap = std::min<uint64_t>(cap, list_want(scan[0], out));
+    scan[0].list_cap = cap;
+  }
+}
+
+// The plain path to completion (blocking), with the retry policy of run_ranges.
+sv_status run_plain(sv_ctx *c, std::vector<RangeSpec> &sieve, std::vector<RangeSpec> &scan, sv_range_result *out,
+                    cudaStream_t st) {
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    sv_status s = plain_enqueue(c, sieve, scan, st);
+    if (s) return s;
+    Collect what;
+    bool sr;
+    if ((s = plain_collect(c, sieve, scan, out, st, &what, &sr))) return s;
+    if (what == kDone) {
+      c->last_h2d = c->ws.h2d_bytes + (sieve.empty() ? 0 : c->ws_sieve.h2d_bytes);
+      c->last_d2h = c->ws.d2h_bytes + (sieve.empty() ? 0 : c->ws_sieve.d2h_bytes);
+      c->ws.force_general = false;
+      return SV_OK;
+    }
+    plain_retry(c, what, sr, sieve, scan, out);
+  }
+  return SV_EOVERFLOW;
+}
+
 sv_status launch_ranges_async(sv_ctx *c, std::vector<RangeSpec> &specs, Workspace &ws, cudaStream_t st) {
   sv_status s = ensure_tile_smem(c);
   if (s) return s;
@@ -923,6 +1033,8 @@ void sv_destroy(sv_ctx *c) {
   c->server = nullptr;
   cudaStreamSynchronize(c->stream);
   c->ws.release_all();
+  c->ws_sieve.release_all();
+  c->plain_bitmap.release();
   cudaFree(c->d_p);
   cudaFree(c->d_mu);
   cudaFree(c->d_inv);
@@ -1100,6 +1212,7 @@ sv_status sv_launch_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, siz
   if ((s = enqueue_graph(c, g, c->ws, c->stream))) return s;
   c->pending = true;
   c->pending_graph = true;
+  c->pending_plain = false;
   c->pending_specs.swap(specs);
   return SV_OK;
 }
@@ -1108,7 +1221,7 @@ sv_status sv_fetch_batch(sv_ctx *c, sv_range_result *out, size_t count) {
   if (!c || (count && !out)) return SV_EINVAL;
   SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
-  if (!c->pending || count != c->pending_specs.size()) return SV_EINVAL;
+  if (!c->pending || c->pending_plain || count != c->pending_specs.size()) return SV_EINVAL;
   c->pending = false;
   std::vector<sv_range_result *> outs(count);
   for (size_t i = 0; i < count; ++i) outs[i] = &out[i];
@@ -1184,6 +1297,7 @@ sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_
   if ((s = plan(c, specs, g, c->ws))) return s;
   if ((s = enqueue(c, g, c->ws, c->stream))) return s;
   c->pending = true;
+  c->pending_plain = false;
   c->pending_specs = specs;
   return SV_OK;
 }
@@ -1194,6 +1308,21 @@ sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
   std::lock_guard<std::mutex> lk(c->mu);
   if (!c->pending || c->pending_specs.size() != 1) return SV_EINVAL;
   c->pending = false;
+  if (c->pending_plain) {
+    c->pending_plain = false;
+    Collect what;
+    bool sr;
+    sv_status s = plain_collect(c, c->pending_sieve_specs, c->pending_specs, out, c->stream, &what, &sr);
+    if (s) return s;
+    if (what != kDone) {  // an overflow: repeat both passes with grown buffers, blocking
+      plain_retry(c, what, sr, c->pending_sieve_specs, c->pending_specs, out);
+      return run_plain(c, c->pending_sieve_specs, c->pending_specs, out, c->stream);
+    }
+    c->ws.force_general = false;
+    c->last_h2d = c->ws.h2d_bytes + c->ws_sieve.h2d_bytes;
+    c->last_d2h = c->ws.d2h_bytes + c->ws_sieve.d2h_bytes;
+    return SV_OK;
+  }
   sv_range_result *outs[1] = {out};
   Collect what;
   sv_status s = collect(c, c->pending_specs, outs, c->ws, c->stream, &what);
@@ -1209,6 +1338,48 @@ sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
   }
   c->last_h2d = c->ws.h2d_bytes;
   c->last_d2h = c->ws.d2h_bytes;
+  return SV_OK;
+}
+
+sv_status sv_verify_range_plain(sv_ctx *c, uint64_t lo, uint64_t hi, sv_range_result *out) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (!out) return SV_EINVAL;
+  if ((s = check_range(c, lo, hi))) return s;
+  SV_ON_DEVICE(c);
+  std::lock_guard<std::mutex> lk(c->mu);
+  const uint64_t n_odd = range_odd_count(lo, hi);
+  uint8_t *d_per_n = nullptr;
+  if (out->per_n_k && n_odd) {
+    if (c->ws.per_n.ensure(n_odd)) return SV_ENOMEM;
+    d_per_n = c->ws.per_n.p;
+  }
+  std::vector<RangeSpec> sieve, scan;
+  if ((s = plain_specs(c, lo, hi, d_per_n, out->list_cap, std::max<uint64_t>(out->fail_cap, 64), sieve, scan)))
+    return s;
+  if ((s = run_plain(c, sieve, scan, out, c->stream))) return s;
+  if (d_per_n) {
+    if (cudaMemcpyAsync(out->per_n_k, d_per_n, n_odd, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return SV_ECUDA;
+    c->last_d2h += n_odd;
+  }
+  return SV_OK;
+}
+
+sv_status sv_launch_range_plain(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_k) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if ((s = check_range(c, lo, hi))) return s;
+  SV_ON_DEVICE(c);
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<RangeSpec> sieve, scan;
+  if ((s = plain_specs(c, lo, hi, d_per_n_k, c->cfg.list_capacity, 1024, sieve, scan))) return s;
+  if ((s = plain_enqueue(c, sieve, scan, c->stream))) return s;
+  c->pending = true;
+  c->pending_plain = true;
+  c->pending_specs.swap(scan);
+  c->pending_sieve_specs.swap(sieve);
   return SV_OK;
 }
 

@@ -56,6 +56,8 @@ struct RangeSpec {
   uint64_t fail_cap = 0;
   bool sieve_only = false;
   uint32_t *bitmap_out = nullptr;
+  const uint32_t *bitmap_in = nullptr;  // scan pass of the plain path: windows from this bitmap
+  int64_t bitmap_w0 = 0;                // absolute word held by bitmap_in[0]
 };
 
 // What a captured launch graph depends on (compared bytewise).
@@ -100,6 +102,8 @@ struct Workspace {
   bool any_per_n = false;
   bool ordered = false;        // the planned launch produces ordered lists (tile kernel mode 0)
   bool force_general = false;  // repeat with the unordered list path (a tile's staging overflowed)
+  bool all_from_bitmap = false;  // every range reads its windows from a bitmap: no bucket fill
+  int tile_kernel_id = 2;        // per-kernel timing id of this workspace's tile kernel launches
   uint64_t j_max = 0;  // largest odd-multiplier count of the launch (bucket fill by j)
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
   // the captured launch graph and what it was captured for
@@ -156,10 +160,16 @@ struct sv_ctx {
   std::vector<double> inv_sq_suffix;  // sum over j >= i of 1/p_j^2 (bucket sizing only)
   std::atomic<size_t> smem_set{0};  // dynamic smem the tile kernel was configured for
   sv::Workspace ws;
+  // the plain (unfused) path: the sieve pass's workspace and the bitmap
+  // between the two passes
+  sv::Workspace ws_sieve;
+  sv::DBuf<uint32_t> plain_bitmap;
   // device-resident pending launch
   bool pending = false;
   bool pending_graph = false;
+  bool pending_plain = false;
   std::vector<sv::RangeSpec> pending_specs;
+  std::vector<sv::RangeSpec> pending_sieve_specs;
   // per-kernel timing with events on the launching stream (sv_kernel_timing)
   uint32_t kprof = 0;  // kernel ids timed with events (bit i: id i)
   struct KEv {
@@ -191,7 +201,6 @@ sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_rang
 // Points already staged in ws.h_points: upload, test, download into
 // ws.h_points_out (no wait).
 sv_status launch_points_async(sv_ctx *c, uint64_t count, Workspace &ws, cudaStream_t st);
-void set_interval_roots(ReqDesc &d, uint32_t mw);
 uint64_t range_odd_count(uint64_t lo, uint64_t hi);
 // Device list entries to reserve for a range of n_odd odd n with threshold T
 // (twice the heuristic expectation plus slack, at most cap); an overflow is

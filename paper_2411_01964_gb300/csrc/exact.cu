@@ -13,21 +13,10 @@
 // prime table; the warp stops at the first p with p^2 | s.
 #include <cuda_runtime.h>
 
+#include "strike.h"
 #include "sv_internal.h"
 
 namespace sv {
-
-// floor(sqrt(r)) by Newton's iteration from above (integer only).
-__device__ __forceinline__ uint64_t isqrt_u64(uint64_t r) {
-  if (r < 2) return r;
-  const int bits = 64 - __clzll((long long)r);
-  uint64_t x = 1ull << ((bits + 1) >> 1);  // x >= sqrt(r)
-  for (;;) {
-    const uint64_t y = (x + r / x) >> 1;
-    if (y >= x) return x;
-    x = y;
-  }
-}
 
 // Warp-cooperative: is the odd number s >= 1 squarefree?  All 32 lanes call
 // it with the same s and get the same answer.

@@ -202,7 +202,6 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
   const uint64_t nwords = (d.jhi > d.jlo) ? (uint64_t)(d.wend - d.w0) : 0;
   const uint64_t nt = (nwords + g.tw - 1) / g.tw;
   d.n_primes = hi > 1 ? primes_upto_of(c, host_isqrt(hi - 1)) : 0;
-  set_interval_roots(d, g.mw);
   d.list_cap = kNaList;
   d.fail_cap = kNaFail;
 
@@ -240,7 +239,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
       return SV_ECUDA;
     // the array keeps the previous call's contents: the counters, the result
     // slot and the bucket counts are cleared on the device first
-    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, st) != cudaSuccess) return SV_ECUDA;
+    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, d_req, g.mw, st) != cudaSuccess) return SV_ECUDA;
     c->launches++;
     if (d.n_primes > g.i_large) {
       BucketArgs b{};

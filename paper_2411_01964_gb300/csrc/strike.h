@@ -24,4 +24,17 @@ __device__ __forceinline__ uint64_t first_strike(uint64_t A, uint64_t q, uint64_
   return (c >= r) ? (c - r) : (c + q - r);
 }
 
+// floor(sqrt(r)) by Newton's iteration from above (integer only): the start
+// 2^ceil(bits/2) is at least the root, and the iterates fall to it.
+__device__ __forceinline__ uint64_t isqrt_u64(uint64_t r) {
+  if (r < 2) return r;
+  const int bits = 64 - __clzll((long long)r);
+  uint64_t x = 1ull << ((bits + 1) >> 1);
+  for (;;) {
+    const uint64_t y = (x + r / x) >> 1;
+    if (y >= x) return x;
+    x = y;
+  }
+}
+
 }  // namespace sv

@@ -23,6 +23,7 @@ enum : uint32_t {
   kStStragOverflow = 1u << 1,   // straggler queue full: rerun with a larger one
   kStBadTile = 1u << 2,         // a tile index failed a bounds check
   kStListStage = 1u << 3,       // a tile's staged list was full: rerun with the unordered list path
+  kStTimeout = 1u << 4,         // a bounded wait for a bulk copy ran out (SV_ETIMEDOUT)
 };
 
 // List entries (mink >= T) a tile stages for the ordered list (mode 0): the
@@ -63,10 +64,15 @@ struct ReqDesc {
   uint32_t sieve_only;  // 1: write the sieved words to bitmap_out, no scan
   // floor(sqrt(2A)) and floor(sqrt(2E - 1)) for the window bits [A, E) the
   // bucket fill covers (A = 32 max(w0 - mw, 0), E = jhi): the integer square
-  // roots of the ends of its odd-multiple interval, one per range
+  // roots of the ends of its odd-multiple interval, set by the init kernel
   uint32_t sq_lo, sq_hi;
   uint32_t pad;
   uint32_t *bitmap_out; // sieve_only: word (a - w0) receives absolute word a
+  // scan from device memory (the plain path): bitmap word (a - bitmap_w0)
+  // holds absolute word a for every word of the range's windows; the tile
+  // copies its window from there instead of sieving it (null: sieve)
+  const uint32_t *bitmap_in;
+  int64_t bitmap_w0;
 };
 
 // Per-range aggregates, accumulated with atomics.
@@ -181,7 +187,8 @@ struct CompactArgs {
 
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
-                        uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, cudaStream_t st);
+                        uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, ReqDesc *reqs, uint32_t mw,
+                        cudaStream_t st);
 cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st);
 // n_large_max, n_reqs: upper bounds of the launch's bucket primes and ranges;
 // j_max: the largest odd multiplier any range needs for the primes >= p_hyb.
@@ -197,7 +204,7 @@ size_t tile_static_smem();
 cudaError_t launch_stragglers(const StragArgs &a, uint32_t grid, cudaStream_t st);
 cudaError_t launch_points(PrimeTab pt, const uint64_t *pts, uint64_t count, uint8_t *out,
                           uint32_t grid, cudaStream_t st);
-uint64_t host_isqrt(uint64_t x);  // floor(sqrt(x)), integer only (host)
+uint64_t host_isqrt(uint64_t x);  // floor(sqrt(x)), exact (host)
 cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, uint64_t **d_inv,
                               uint64_t **d_lim, uint32_t **d_bits, uint64_t *bits_words, uint32_t *n,
                               uint32_t *n_div, cudaStream_t st);

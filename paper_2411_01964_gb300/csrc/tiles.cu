@@ -35,11 +35,19 @@
 //              result slot (Sec. 3 "Collecting the results"), and the tile's
 //              listed n (mink >= T) into its staging slot for the ordered
 //              list (list_compact_kernel).
-// The bitmap never leaves shared memory.
+// The bitmap never leaves shared memory on this fused path.
+//
+// The plain (unfused) path runs the same kernel twice: a sieve pass
+// (sieve_only ranges: phases 1-2, then the window's core words go to a bitmap
+// in device memory with one bulk store per tile) and a scan pass (bitmap_in
+// ranges: the tile fills its window from that bitmap with one bulk load, then
+// phases 3-4).  Both bulk copies are cp.async.bulk (the TMA unit), tracked by
+// an mbarrier (loads) or a bulk group (stores).
 #include <cuda_runtime.h>
 
 #include "strike.h"
 #include "sv_internal.h"
+#include "tma.h"
 
 namespace sv {
 
@@ -154,12 +162,22 @@ __device__ __forceinline__ void strike(uint32_t *win, uint32_t b) {
 }
 
 // ---------------------------------------------------------------------------
-// init: zero the launch's counters, result slots, bucket and staged-list counts.
+// init: zero the launch's counters, result slots, bucket and staged-list
+// counts; give each range the integer square roots of its bucket-fill
+// interval ends (ReqDesc::sq_lo, sq_hi) for the multiplier items.
 // ---------------------------------------------------------------------------
-__global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count, uint32_t *stage_cnt) {
+__global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count, uint32_t *stage_cnt,
+                            ReqDesc *reqs, uint32_t mw) {
   const uint32_t n_slots = hdr->n_reqs, n_tiles = hdr->total_tiles;
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gs = gridDim.x * blockDim.x;
+  for (uint32_t r = gid; r < n_slots; r += gs) {
+    ReqDesc &R = reqs[r];
+    const int64_t ws = R.w0 - (int64_t)mw;
+    const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);  // the fill's window bits [A, E = jhi)
+    R.sq_lo = (uint32_t)isqrt_u64(2 * A);
+    R.sq_hi = R.jhi ? (uint32_t)isqrt_u64(2 * R.jhi - 1) : 0u;
+  }
   for (uint32_t i = gid; i < n_tiles; i += gs) {
     bucket_count[i] = 0;
     if (stage_cnt) stage_cnt[i] = 0;
@@ -180,13 +198,14 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
 }
 
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
-                        uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, cudaStream_t st) {
+                        uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, ReqDesc *reqs, uint32_t mw,
+                        cudaStream_t st) {
   uint64_t work = (uint64_t)n_slots * kMaxK;
   if (n_tiles > work) work = n_tiles;
   uint32_t grid = (uint32_t)((work + 255) / 256);
   if (grid < 1) grid = 1;
   if (grid > 1024) grid = 1024;
-  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt);
+  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt, reqs, mw);
   return cudaGetLastError();
 }
 
@@ -218,7 +237,12 @@ struct ScanShared {
   uint8_t lst_k[kLstCap];
   uint32_t sparse_off[kMaxSparse]; // first struck bit of each sparse prime (>= nbits: none)
   uint32_t sparse_q[kMaxSparse];
+  uint64_t load_bar;               // mbarrier of the scan pass's bulk window loads
 };
+
+// A bounded wait (about one second at the maximum clock) for the window's bulk
+// load; the outcome is the same for every thread of the block.
+constexpr long long kBulkWaitCycles = 2000000000ll;
 
 // Record the n of hit (mink = k, k >= T) in the range's list and first_n.
 __device__ __noinline__ void list_append(const TileArgs &a, const ReqDesc &R, uint32_t hit,
@@ -607,6 +631,12 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     sh.hist[tid] = 0ull;
     sh.first[tid] = kNoN;
   }
+  if (tid == 0) {
+    mbar_init(&sh.load_bar, 1);
+    fence_mbar_init();
+  }
+  uint32_t load_parity = 0;     // phase parity of the next bulk window load
+  bool store_pending = false;   // thread 0: a bulk store may still read the window
   build_stamp_tables<NS>(stab);
   const uint32_t T = 32u * g.tw;  // a window starts T bits above the previous one
   if (tid == 0) {
@@ -622,6 +652,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
   __syncthreads();
 
   for (;;) {
+    if (store_pending) {  // thread 0 only: the window is overwritten below
+      bulk_wait_read_all();
+      store_pending = false;
+    }
     if (tid == 0) {
       const uint32_t t = sh.next_tile;
       uint32_t fresh = sh.tile == 0xFFFFFFFFu || t != sh.tile + 1u;  // not the previous tile's successor
@@ -649,7 +683,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     }
     __syncthreads();
     const uint32_t gt = sh.tile;
-    if (gt >= total) break;
+    if (gt >= total) {
+      if (tid == 0) bulk_wait_all();  // the last bulk stores complete before the block exits
+      break;
+    }
     const ReqDesc &R = sh.req;
     const uint32_t t = gt - R.tile_base;
     const bool fresh = sh.fresh != 0;
@@ -682,6 +719,48 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     if (tid == 0 && !R.sieve_only)
       for (uint32_t k = 1; k <= kfirst; ++k) known[k - 1] = __ldcg(&a.slots[R.slot].first_n[k]);
 
+    if (R.bitmap_in) {
+      // ---- scan pass of the plain path: the window from device memory ------
+      const uint32_t nz0 = (wstart < 0) ? (uint32_t)min((int64_t)nwords, -wstart) : 0u;
+      for (uint32_t i = tid; i < nz0; i += S) win[i] = 0u;  // integers below 1
+      const uint32_t cnt = nwords - nz0;
+      const uint32_t *src = R.bitmap_in + (wstart + (int64_t)nz0 - R.bitmap_w0);
+      // a bulk copy needs both addresses 16-byte aligned and a 16-byte
+      // multiple; the rounded copy must stay inside the window (tw + mw
+      // words), and the bitmap is allocated with 4 words of room behind it
+      const uint32_t cnt4 = (cnt + 3u) & ~3u;
+      const bool bulk = cnt && (nz0 & 3u) == 0u && ((uintptr_t)src & 15u) == 0u && nz0 + cnt4 <= g.tw + g.mw;
+      if (bulk) {
+        if (tid == 0) {
+          fence_proxy_async_smem();  // the previous tile's reads of the window come first
+          const uint32_t bytes = 4u * cnt4;
+          mbar_arrive_expect_tx(&sh.load_bar, bytes);
+          bulk_load(win + nz0, src, bytes, &sh.load_bar);
+        }
+      } else {
+        for (uint32_t i = tid; i < cnt; i += S) win[nz0 + i] = src[i];
+      }
+      if (tid == 0) {
+        uint32_t need = 0;
+        for (uint32_t k = 1; k <= kfirst; ++k)
+          if (known[k - 1] > n_first) need |= 1u << k;
+        sh.need = need;
+      }
+      if (bulk) {
+        bool ok = mbar_wait_bounded(&sh.load_bar, load_parity, kBulkWaitCycles);
+        if (__syncthreads_or(!ok)) {
+          // the copy did not arrive in time: report it, wait once more for
+          // the copy in flight (it writes into this block's shared memory),
+          // and stop this block
+          if (tid == 0) atomicOr(&a.hdr->status, kStTimeout);
+          ok = mbar_wait_bounded(&sh.load_bar, load_parity, kBulkWaitCycles);
+          __syncthreads_or(!ok);
+          return;
+        }
+        load_parity ^= 1u;
+      }
+      __syncthreads();
+    } else {
     // ---- 1. stamp the smallest primes; the dense primes' first strikes -------
     if (warp < kMaxDense / 32) {  // blockDim.x >= 128: warps 0..3 exist
       const uint32_t d = 32u * warp + lane;
@@ -774,6 +853,7 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       }
     }
     __syncthreads();
+    }  // sieve (phases 1-2) or window from device memory
 
     // the next tile's index (the chunk's next tile, else a new chunk's first),
     // fetched while this tile is scanned
@@ -788,12 +868,26 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
     }
 
     if (R.sieve_only) {
-      // ---- Algorithm 1 alone: write the core words ------------------------
-      for (uint32_t i = g.mw + tid; i < nwords; i += S) {
-        const int64_t aw = wstart + (int64_t)i;
-        const uint32_t v = valid_mask(32ull * (uint64_t)aw, R.jlo, R.jhi);
-        R.bitmap_out[aw - R.w0] = win[i] & v;
+      // ---- Algorithm 1 alone: the core words to the bitmap ----------------
+      // bits outside [jlo, jhi) are cleared first (only the range's first and
+      // last words have any); then one bulk store of the 16-byte multiple,
+      // plain stores for the rest (or everything, for an unaligned buffer)
+      const uint32_t cnt = nwords - g.mw;
+      uint32_t *dst = R.bitmap_out + (tws - R.w0);
+      if (tid == 0) {
+        win[g.mw] &= valid_mask(32ull * (uint64_t)tws, R.jlo, R.jhi);
+        win[nwords - 1] &= valid_mask(32ull * (uint64_t)(twe - 1), R.jlo, R.jhi);
       }
+      fence_proxy_async_smem();  // the window's strikes and masks before the bulk store
+      __syncthreads();
+      const bool bulk = cnt >= 4u && ((uintptr_t)dst & 15u) == 0u && (g.mw & 3u) == 0u;  // win + mw aligned
+      const uint32_t nbulk = bulk ? (cnt & ~3u) : 0u;
+      if (bulk && tid == 0) {
+        bulk_store(dst, win + g.mw, 4u * nbulk);
+        bulk_commit();
+        store_pending = true;
+      }
+      for (uint32_t i = nbulk + tid; i < cnt; i += S) dst[i] = win[g.mw + i];
     } else {
       // ---- 3. word-parallel Algorithm 2 ------------------------------------
       // core words whose 32 bits are all valid: window indices [ifl, ifl+nfull)
