@@ -181,9 +181,15 @@ def measured_traffic(n_odd: int):
     return t["dram_bytes_per_odd_n"] * n_odd
 
 
-def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3) -> dict:
+CONFIG_KNOBS = ("tile_log2", "threads", "ctas_per_sm", "margin_log2", "stamp_primes", "large_prime_min",
+                "mult_prime_log2", "bucket_capacity")
+
+
+def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3, tune: bool = True) -> dict:
     """Config 4: 4096 ranges (seed 7) as one batched graph launch, against the
-    plain path (one range per launch, back to back on the same stream)."""
+    plain path (one range per launch, back to back on the same stream); then
+    the autotuner on a sample of the batch (every eighth range), and the batch
+    again with the configuration it chose."""
     import torch
     from paper_2411_01964_gb300 import Verifier
     c = v0.config
@@ -194,18 +200,24 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3) -> dict:
     his = [b for _, b in reqs]
     n_odd = sum(odd_count(a, b) for a, b in reqs)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    v.launch_batch(los, his)  # warm-up: captures the graph
-    first = v.fetch_batch(list_cap=16)
-    bt = []
-    for _ in range(reps):
-        flush.zero_()
-        ev[0].record(stream)
-        v.launch_batch(los, his)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
-        bt.append(ev[0].elapsed_time(ev[1]))
-        res = v.fetch_batch(list_cap=16)
-    assert [r.hist for r in res] == [r.hist for r in first]
+
+    def time_batch():
+        v.launch_batch(los, his)  # warm-up: captures the graph
+        first = v.fetch_batch(list_cap=16)
+        bt = []
+        for _ in range(reps):
+            flush.zero_()
+            ev[0].record(stream)
+            v.launch_batch(los, his)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            bt.append(ev[0].elapsed_time(ev[1]))
+            res = v.fetch_batch(list_cap=16)
+        assert [r.hist for r in res] == [r.hist for r in first]
+        return sum(bt) / len(bt), res
+
+    ms_default, res = time_batch()
+    cfg_default = {k: getattr(v.config, k) for k in CONFIG_KNOBS}
     # plain path: one launch per range
     flush.zero_()
     ev[0].record(stream)
@@ -216,12 +228,27 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3) -> dict:
     pt = ev[0].elapsed_time(ev[1])
     last = v.fetch_range(list_cap=16)
     assert last.hist == res[-1].hist, "plain and batched paths disagree"
-    ms = sum(bt) / len(bt)
+    out = {"workload": f"{n_requests} ranges, seed 7 (starts odd in [2^30, 2^50), lengths 2^10..2^28)",
+           "odd_n": n_odd, "ms": ms_default, "value": n_odd / (ms_default / 1e3), "unit": UNIT,
+           "config": cfg_default, "plain_ms": pt, "plain_value": n_odd / (pt / 1e3),
+           "speedup_vs_plain": pt / ms_default, "graph": "one captured graph, replayed per batch",
+           "timed": "CUDA events around the launch call: host planning, descriptor upload and kernels"}
+    if tune:
+        t0 = time.perf_counter()
+        v.autotune_batch(los[::8], his[::8])
+        tune_s = time.perf_counter() - t0
+        ms_tuned, res_t = time_batch()
+        assert [r.hist for r in res_t] == [r.hist for r in res], "the tuned configuration changed a result"
+        out["default"] = {"ms": ms_default, "value": n_odd / (ms_default / 1e3), "config": cfg_default}
+        out["tuned"] = {"ms": ms_tuned, "value": n_odd / (ms_tuned / 1e3),
+                        "config": {k: getattr(v.config, k) for k in CONFIG_KNOBS},
+                        "tuned_on": f"every eighth range of the batch ({len(los[::8])} ranges)",
+                        "tuning_s": tune_s}
+        if ms_tuned < ms_default:
+            out.update(ms=ms_tuned, value=n_odd / (ms_tuned / 1e3), config=out["tuned"]["config"],
+                       speedup_vs_plain=pt / ms_tuned)
     v.close()
-    return {"workload": f"{n_requests} ranges, seed 7 (starts odd in [2^30, 2^50), lengths 2^10..2^28)",
-            "odd_n": n_odd, "ms": ms, "value": n_odd / (ms / 1e3), "unit": UNIT,
-            "plain_ms": pt, "plain_value": n_odd / (pt / 1e3),
-            "speedup_vs_plain": pt / ms, "graph": "one captured graph, replayed per batch"}
+    return out
 
 
 def bench_plain(v, stream, flush, lo: int, hi: int, steps: int, fused: dict, hbm_gbs: float | None) -> dict:
@@ -409,6 +436,7 @@ def main() -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=4096)
     ap.add_argument("--serve-seconds", type=float, default=1.5)
@@ -571,7 +599,7 @@ def main() -> int:
                  "ms": total_ms / args.steps}
         line["plain_hbm"] = bench_plain(v, stream, flush, lo, hi, min(args.steps, 20), fused, drv.get("hbm_gbs"))
     if rank == 0 and world == 1 and not args.no_batch:
-        line["batched"] = bench_batch(v, stream, flush, args.batch_requests)
+        line["batched"] = bench_batch(v, stream, flush, args.batch_requests, tune=not args.no_tune)
     if rank == 0 and world == 1 and not args.no_serve:
         line["served"] = bench_serving(stream, args.serve_seconds, line.get("batched"))
     if rank == 0:

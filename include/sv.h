@@ -89,7 +89,10 @@ typedef struct sv_config {
     uint32_t list_stage_capacity;/* listed n a tile may stage for the ordered list (1..128; 0 = 128).
                                     A tile with more repeats the launch through the unordered list
                                     path; results never depend on it (small values exercise that path) */
-    uint32_t reserved0;
+    uint32_t mult_prime_log2;    /* multiplier threshold: bucket primes p >= 2^mult_prime_log2 reach the
+                                    buckets by enumerating the odd multipliers j of j p^2 in the range
+                                    (cheap for many short ranges far up); smaller bucket primes take one
+                                    Barrett reduction per range (10..31; 0 = 18) */
 } sv_config;
 
 /*
@@ -265,11 +268,19 @@ sv_status sv_min_k_device(sv_ctx *ctx, const uint64_t *d_points, size_t count, u
 sv_status sv_synchronize(sv_ctx *ctx);
 
 /*
- * Autotuner: times candidate tile sizes, thread counts, look-back margins and
- * large-prime thresholds on [lo, hi) (a sample of the target workload) and
- * keeps the fastest in the context.  Never changes results.
+ * Autotuner (coordinate descent, two rounds): times candidate values of each
+ * knob in turn -- tile shape (tile_log2, threads, ctas_per_sm), stamped
+ * primes, look-back margin, bucket threshold (large_prime_min), multiplier
+ * threshold (mult_prime_log2) and bucket depth (bucket_capacity) -- with the
+ * others held, and keeps the fastest configuration in the context (and in
+ * *chosen, if not NULL).  The work timed is the device time (CUDA events on the
+ * context's stream, best of three after a warm-up) of [lo, hi) as one launch
+ * (sv_autotune) or of the `count` ranges as one batched launch
+ * (sv_autotune_batch), a sample of the target workload.  Never changes
+ * results.  Errors: as sv_verify_range / sv_verify_batch.
  */
 sv_status sv_autotune(sv_ctx *ctx, uint64_t lo, uint64_t hi, sv_config *chosen);
+sv_status sv_autotune_batch(sv_ctx *ctx, const uint64_t *lo, const uint64_t *hi, size_t count, sv_config *chosen);
 
 /*
  * Serving.  sv_submit admits a range or point request into the request loop

@@ -130,6 +130,9 @@ class Verifier:
     def autotune(self, lo: int, hi: int) -> B.sv_config:
         return B.sv_autotune(self.ctx, lo, hi)
 
+    def autotune_batch(self, los, his) -> B.sv_config:
+        return B.sv_autotune_batch(self.ctx, np.asarray(los, dtype=np.uint64), np.asarray(his, dtype=np.uint64))
+
     def prime_count(self) -> tuple[int, int]:
         return B.sv_prime_count(self.ctx)
 

@@ -29,7 +29,7 @@ class sv_config(ctypes.Structure):
     _fields_ = [("tile_log2", u32), ("margin_log2", u32), ("threads", u32), ("large_prime_min", u32),
                 ("bucket_capacity", u32), ("record_k_threshold", u32), ("ctas_per_sm", u32),
                 ("stamp_primes", u32), ("list_capacity", u64), ("device_mem_budget", u64),
-                ("cuda_stream", ctypes.c_void_p), ("list_stage_capacity", u32), ("reserved0", u32)]
+                ("cuda_stream", ctypes.c_void_p), ("list_stage_capacity", u32), ("mult_prime_log2", u32)]
 
 
 class sv_range_result(ctypes.Structure):
@@ -82,6 +82,7 @@ _SIGS = {
     "sv_fetch_range": (ctypes.c_int, [_CTX, P(sv_range_result)]),
     "sv_synchronize": (ctypes.c_int, [_CTX]),
     "sv_autotune": (ctypes.c_int, [_CTX, u64, u64, P(sv_config)]),
+    "sv_autotune_batch": (ctypes.c_int, [_CTX, P(u64), P(u64), ctypes.c_size_t, P(sv_config)]),
     "sv_submit": (ctypes.c_int, [_CTX, P(sv_request), P(u64)]),
     "sv_poll": (ctypes.c_int, [_CTX, u64, ctypes.c_int64]),
     "sv_cancel": (ctypes.c_int, [_CTX, u64]),
@@ -246,6 +247,15 @@ def sv_synchronize(ctx) -> int:
 def sv_autotune(ctx, lo: int, hi: int) -> sv_config:
     c = sv_config()
     check(load().sv_autotune(ctx, lo, hi, ctypes.byref(c)), "sv_autotune")
+    return c
+
+
+def sv_autotune_batch(ctx, lo: np.ndarray, hi: np.ndarray) -> sv_config:
+    lo = np.ascontiguousarray(lo, dtype=np.uint64)
+    hi = np.ascontiguousarray(hi, dtype=np.uint64)
+    c = sv_config()
+    check(load().sv_autotune_batch(ctx, lo.ctypes.data_as(P(u64)), hi.ctypes.data_as(P(u64)), len(lo),
+                                   ctypes.byref(c)), "sv_autotune_batch")
     return c
 
 

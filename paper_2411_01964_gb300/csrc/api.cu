@@ -116,6 +116,8 @@ sv_status normalise_config(sv_ctx *c, sv_config *k) {
   const size_t smem = 4 * (tw + mw);
   if (c->smem_optin && smem + tile_static_smem() + 1024 > c->smem_optin) return SV_EINVAL;  // window + static
   if (k->large_prime_min == 0) k->large_prime_min = 1u << ((k->tile_log2 + 1) / 2);
+  if (k->mult_prime_log2 == 0) k->mult_prime_log2 = kMultPrimeLog2;
+  if (k->mult_prime_log2 < 10 || k->mult_prime_log2 > 31) return SV_EINVAL;
   return SV_OK;
 }
 
@@ -157,9 +159,9 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   if (il < g.i_dense) il = g.i_dense;
   if (il > g.i_dense + (uint32_t)kMaxSparsePrimes) il = g.i_dense + (uint32_t)kMaxSparsePrimes;
   g.i_large = il;
-  // primes >= 2^kMultPrimeLog2 reach the buckets by enumerating their odd
+  // primes >= 2^mult_prime_log2 reach the buckets by enumerating their odd
   // multipliers (the multiplier items of bucket_fill_kernel)
-  uint32_t ih = primes_upto(c, (1u << kMultPrimeLog2) - 1);
+  uint32_t ih = primes_upto(c, (1ull << k.mult_prime_log2) - 1);
   if (ih < il) ih = il;
   g.i_hyb = ih;
   g.p_hyb = ih < c->n_primes ? c->h_p[ih] : 0xFFFFFFFFu;
@@ -1449,69 +1451,178 @@ sv_status sv_set_config(sv_ctx *c, const sv_config *cfg) {
   return SV_OK;
 }
 
-// Times a grid of tile sizes / thread counts / CTAs per SM / margins /
-// large-prime thresholds on [lo, hi) and keeps the fastest configuration.
+}  // extern "C"
+
+namespace sv {
+
+// ---- autotuner ---------------------------------------------------------------
+
+// Device time of one launch of `specs` under the context's current
+// configuration: a warm-up launch (it sizes the buffers and captures the
+// graph), then the best of three, each bracketed by CUDA events on the
+// context's stream around the descriptor upload and the kernels.
+sv_status time_launch(sv_ctx *c, const std::vector<RangeSpec> &specs0, double *best_ms) {
+  std::vector<RangeSpec> specs = specs0;
+  sv_status s = run_ranges(c, specs, nullptr, c->stream, c->ws, true);
+  if (s) return s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return SV_ECUDA;
+  }
+  double best = 1e300;
+  for (int rep = 0; rep < 3 && !s; ++rep) {
+    Geometry g = make_geometry(c, max_span_bits(c, specs));
+    if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
+    if ((s = plan(c, specs, g, c->ws))) break;
+    if (cudaEventRecord(a, c->stream) != cudaSuccess) s = SV_ECUDA;
+    if (!s) s = enqueue_graph(c, g, c->ws, c->stream);
+    if (!s && cudaEventRecord(b, c->stream) != cudaSuccess) s = SV_ECUDA;
+    Collect what = kDone;
+    if (!s) s = collect(c, specs, nullptr, c->ws, c->stream, &what);
+    if (s) break;
+    if (what != kDone) {  // the warm-up grew everything: this launch reported an overflow anyway
+      s = run_ranges(c, specs, nullptr, c->stream, c->ws, true);
+      continue;
+    }
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) s = SV_ECUDA;
+    else if (ms < best) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *best_ms = best;
+  return s;
+}
+
+// Coordinate descent over the knobs, two rounds; the context keeps the best.
+sv_status tune(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_config *chosen) {
+  const sv_config base = c->cfg;
+  sv_config best = base;
+  double best_t = 1e300;
+  // times candidate k (skipped when invalid or when its CTAs cannot be resident)
+  auto eval = [&](sv_config k, double *t) -> sv_status {
+    *t = 1e300;
+    if (normalise_config(c, &k)) return SV_OK;
+    const size_t smem = 4ull * ((1ull << (k.tile_log2 - 5)) + (1ull << (k.margin_log2 - 6)));
+    if (k.ctas_per_sm * (smem + tile_static_smem() + 1024) > c->smem_optin + 1024 ||
+        (size_t)k.ctas_per_sm * k.threads > 2048)
+      return SV_OK;
+    c->cfg = k;
+    c->ws.bucket_cap = 0;
+    c->ws_sieve.bucket_cap = 0;
+    sv_status s = time_launch(c, specs, t);
+    if (s == SV_ENOMEM || s == SV_EOVERFLOW) {  // this candidate does not fit: skip it
+      *t = 1e300;
+      return SV_OK;
+    }
+    return s;
+  };
+  auto consider = [&](const sv_config &k) -> sv_status {
+    double t;
+    sv_status s = eval(k, &t);
+    if (!s && t < best_t) {
+      best_t = t;
+      best = c->cfg;
+    }
+    return s;
+  };
+  sv_status s = consider(base);
+  struct Shape {
+    uint32_t tile_log2, threads, ctas;
+  };
+  const Shape shapes[] = {{19, 512, 2}, {18, 512, 2}, {18, 256, 3}, {20, 1024, 1}, {19, 1024, 1}, {17, 256, 4}};
+  const uint32_t stamps[] = {2, 4, 6, 8};
+  const uint32_t margins[] = {12, 13, 14, 16};
+  const uint32_t lpmins[] = {512, 1024, 2048, 4096, 8192, 16384};
+  const uint32_t mults[] = {15, 16, 17, 18, 19, 20, 21};
+  for (int round = 0; round < 2 && !s; ++round) {
+    for (const Shape &sh : shapes) {
+      if (s) break;
+      sv_config k = best;
+      k.tile_log2 = sh.tile_log2;
+      k.threads = sh.threads;
+      k.ctas_per_sm = sh.ctas;
+      if (k.margin_log2 > k.tile_log2 + 1) k.margin_log2 = k.tile_log2 + 1;
+      s = consider(k);
+    }
+    for (uint32_t v : stamps) {
+      if (s) break;
+      sv_config k = best;
+      k.stamp_primes = v;
+      s = consider(k);
+    }
+    for (uint32_t v : margins) {
+      if (s) break;
+      sv_config k = best;
+      k.margin_log2 = v;
+      s = consider(k);
+    }
+    for (uint32_t v : lpmins) {
+      if (s) break;
+      sv_config k = best;
+      k.large_prime_min = v;
+      s = consider(k);
+    }
+    for (uint32_t v : mults) {
+      if (s) break;
+      sv_config k = best;
+      k.mult_prime_log2 = v;
+      s = consider(k);
+    }
+    {  // bucket depth: the automatic estimate, or twice it
+      c->cfg = best;
+      const uint32_t cap_auto = make_geometry(c, max_span_bits(c, specs)).bucket_auto;
+      for (uint32_t v : {0u, 2u * cap_auto}) {
+        if (s) break;
+        sv_config k = best;
+        k.bucket_capacity = v;
+        s = consider(k);
+      }
+    }
+  }
+  c->cfg = s ? base : best;
+  c->ws.bucket_cap = 0;
+  c->ws_sieve.bucket_cap = 0;
+  if (!s && chosen) *chosen = best;
+  return s;
+}
+
+}  // namespace sv
+
+extern "C" {
+
 sv_status sv_autotune(sv_ctx *c, uint64_t lo, uint64_t hi, sv_config *chosen) {
   sv_status s = check_ready(c);
   if (s) return s;
   if ((s = check_range(c, lo, hi))) return s;
   SV_ON_DEVICE(c);
   std::lock_guard<std::mutex> lk(c->mu);
-  const sv_config base = c->cfg;
-  sv_config best = base;
-  double best_t = 1e300;
-  sv_range_result res;
-  std::memset(&res, 0, sizeof(res));
-  sv_range_result *outs[1] = {&res};
-  const uint32_t tiles[] = {18, 19, 20};
-  const uint32_t threads[] = {512, 1024};
-  const uint32_t ctas[] = {1, 2};
-  const uint32_t margins[] = {13, 16};
-  const uint32_t stamps[] = {2, 4, 6, 8};
-  for (uint32_t tl : tiles)
-    for (uint32_t th : threads)
-      for (uint32_t cp : ctas)
-        for (uint32_t ml : margins)
-          for (uint32_t ns : stamps) {
-            sv_config k = base;
-            k.tile_log2 = tl;
-            k.threads = th;
-            k.ctas_per_sm = cp;
-            k.stamp_primes = ns;
-            k.margin_log2 = ml < tl + 1 ? ml : tl + 1;
-            k.large_prime_min = 1u << ((tl + 1) / 2);
-            k.bucket_capacity = 0;
-            const size_t smem = 4ull * ((1ull << (tl - 5)) + (1ull << (k.margin_log2 - 6)));
-            if (cp * (smem + 4096) > c->smem_optin + 4096 || (size_t)cp * th > 2048) continue;
-            if (normalise_config(c, &k)) continue;
-            c->cfg = k;
-            c->ws.bucket_cap = 0;
-            double t = 1e300;
-            for (int rep = 0; rep < 3; ++rep) {
-              std::vector<RangeSpec> specs(1);
-              specs[0].lo = lo;
-              specs[0].hi = hi;
-              specs[0].fail_cap = 16;
-              const auto t0 = std::chrono::steady_clock::now();
-              s = run_ranges(c, specs, outs, c->stream, c->ws, false);
-              const auto t1 = std::chrono::steady_clock::now();
-              if (s) break;
-              const double dt = std::chrono::duration<double>(t1 - t0).count();
-              if (rep > 0 && dt < t) t = dt;  // first run warms up
-            }
-            if (s) {
-              c->cfg = base;
-              return s;
-            }
-            if (t < best_t) {
-              best_t = t;
-              best = k;
-            }
-          }
-  c->cfg = best;
-  c->ws.bucket_cap = 0;
-  if (chosen) *chosen = best;
-  return SV_OK;
+  std::vector<RangeSpec> specs(1);
+  specs[0].lo = lo;
+  specs[0].hi = hi;
+  specs[0].list_cap = list_cap_estimate(range_odd_count(lo, hi), c->cfg.record_k_threshold, c->cfg.list_capacity);
+  specs[0].fail_cap = 16;
+  return tune(c, specs, chosen);
+}
+
+sv_status sv_autotune_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, size_t count, sv_config *chosen) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (count == 0 || !lo || !hi) return SV_EINVAL;
+  for (size_t i = 0; i < count; ++i)
+    if ((s = check_range(c, lo[i], hi[i]))) return s;
+  SV_ON_DEVICE(c);
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::vector<RangeSpec> specs(count);
+  for (size_t i = 0; i < count; ++i) {
+    specs[i].lo = lo[i];
+    specs[i].hi = hi[i];
+    specs[i].list_cap = list_cap_estimate(range_odd_count(lo[i], hi[i]), c->cfg.record_k_threshold,
+                                          c->cfg.list_capacity);
+    specs[i].fail_cap = 16;
+  }
+  return tune(c, specs, chosen);
 }
 
 sv_status sv_submit(sv_ctx *c, const sv_request *req, uint64_t *ticket) {

@@ -213,10 +213,11 @@ constexpr int kMaxDensePrimes = 128;  // must match the tile kernel's shared arr
 constexpr int kDenseMinHits = 4;      // primes with at least this many strikes per window are "dense"
 constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)
 constexpr uint32_t kFillBlocksPerSm = 4;  // resident bucket-fill blocks per SM (the launch bounds)
-// Bucket primes below 2^kMultPrimeLog2 get one Barrett reduction per range;
-// larger ones are found through their odd multipliers j (j p^2 in the range),
-// which costs a few operations per multiplier instead of one reduction per
-// prime, the cheaper way for them when many short ranges lie far up.
+// Bucket primes below 2^mult_prime_log2 (sv_config) get one Barrett reduction
+// per range; larger ones are found through their odd multipliers j (j p^2 in
+// the range), which costs a few operations per multiplier instead of one
+// reduction per prime, the cheaper way for them when many short ranges lie far
+// up.  The default threshold:
 constexpr int kMultPrimeLog2 = 18;
 
 }  // namespace sv

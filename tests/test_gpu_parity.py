@@ -108,6 +108,8 @@ KNOBS = [
     dict(stamp_primes=2),
     dict(stamp_primes=6, tile_log2=19, threads=512, ctas_per_sm=2, margin_log2=13),
     dict(stamp_primes=8, tile_log2=16, record_k_threshold=5),
+    dict(mult_prime_log2=14),                   # nearly all bucket primes through their multipliers
+    dict(mult_prime_log2=24, large_prime_min=4096),  # nearly all through one Barrett reduction each
 ]
 
 
