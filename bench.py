@@ -251,6 +251,63 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3, tune: bool = 
     return out
 
 
+def bench_range(name: str, stream, flush, steps: int, pk: dict, knobs: dict) -> dict:
+    """One more plain single range (its own context), on the headline's timing
+    rules: device time per step with CUDA events, L2 flushed between steps, the
+    tile kernel's own events, and the blocking call with host buffers (e2e)."""
+    import torch
+    from paper_2411_01964_gb300 import Verifier, binding as B
+    lo, hi = WORKLOADS[name]
+    n_odd = odd_count(lo, hi)
+    with Verifier(max_hi=hi + 1, stream=stream.cuda_stream, **knobs) as v:
+        for _ in range(3):
+            v.launch_range(lo, hi)
+            r = v.fetch_range(list_cap=1 << 20)
+        assert sum(r.hist) + r.fail_len == n_odd
+        B.sv_kernel_timing(v.ctx, ["tile"])
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            v.launch_range(lo, hi)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        t_ms, t_n = B.sv_kernel_time(v.ctx, B.KERNEL_IDS["tile"])
+        B.sv_kernel_timing(v.ctx, False)
+        v.fetch_range(list_cap=16)
+        t0 = time.perf_counter()
+        e2e_steps = 3
+        h2d = d2h = 0
+        for _ in range(e2e_steps):
+            rr = v.verify_range(lo, hi, list_cap=1 << 20)
+            a, b = v.last_transfer()
+            h2d += a
+            d2h += b
+        e2e_s = time.perf_counter() - t0
+        assert rr.hist == r.hist
+    tile_s = t_ms / max(t_n, 1) / 1e3
+    achieved = alu_ops_per_odd_n(hi) * n_odd / tile_s
+    strikes = strikes_per_launch(lo, hi, v_cfg(knobs))
+    return {"workload": WORKLOAD_NAMES[name], "lo": lo, "hi": hi, "odd_n": n_odd, "steps": steps,
+            "ms_per_step": ms, "value": n_odd / (ms / 1e3), "unit": UNIT,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": pk["scan_mix_ops_per_s"], "unit": "int32 ops/s",
+                         "frac": achieved / pk["scan_mix_ops_per_s"], "kernel": "tile_kernel (sieve + scan, fused)",
+                         "kernel_avg_ms": tile_s * 1e3, "smem_atomic_frac": strikes / tile_s / pk["smem_atomic_strike_per_s"],
+                         "peak_source": "measured in this run (sv_measure_peaks)"},
+            "e2e": {"value": n_odd * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
+                    "d2h_bytes_per_step": d2h // e2e_steps},
+            "result": {"hist": r.hist[1:16], "kmax": r.kmax, "failures": r.fail_len, "list_len": r.list_len}}
+
+
+def v_cfg(knobs: dict):
+    """The tile geometry knobs strikes_per_launch needs (library defaults when unset)."""
+    class C:
+        tile_log2 = knobs.get("tile_log2") or 19
+        margin_log2 = knobs.get("margin_log2") or 13
+    return C
+
+
 def bench_plain(v, stream, flush, lo: int, hi: int, steps: int, fused: dict, hbm_gbs: float | None) -> dict:
     """The plain (unfused) path on the same range: Algorithm 1 writes the
     bitmap to device memory, Algorithm 2 reads it back.  Device time per step
@@ -299,40 +356,62 @@ def bench_plain(v, stream, flush, lo: int, hi: int, steps: int, fused: dict, hbm
                                            "frac": r_gbs / hbm_gbs if hbm_gbs else None}}}
 
 
-def bench_serving(stream, seconds: float, batched: dict | None) -> dict:
-    """Config 5: Poisson arrivals (seed 11) of the serving mix at several
-    rates; latency from submission to completion, throughput over the run."""
+def bench_serving(stream, n_requests: int, rates, batched: dict | None) -> dict:
+    """Config 5: open-loop Poisson arrivals (seed 11) of the serving mix at each
+    rate, n_requests each.  Every request's structures and buffers are made
+    before the run, so the submitting thread keeps up with the arrival times
+    (it sleeps until shortly before an arrival, then spins).  Latency is the
+    server's own, from submission to completion; throughput is the odd n of
+    all requests over the time from the first arrival to the last completion."""
     from paper_2411_01964_gb300 import Verifier, B
     out = []
-    for rate in (1e2, 1e3, 1e4, 1e5):
-        count = int(min(2000, max(60, rate * seconds)))
-        reqs = inputs.serving_requests(rate, count)
-        odd = sum(odd_count(r.lo, r.hi) if r.kind != "points" else len(r.points) for r in reqs)
-        with Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream) as sv:
-            sv.min_k([3])  # context ready; the server thread starts on the first submit
-            tickets = []
+    with Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream) as sv:
+        # warm-up: a short mix sizes every slot's buffers and captures its graphs
+        warm = [sv.prepare_points(r.points) if r.kind == "points" else sv.prepare_range(r.lo, r.hi, list_cap=64)
+                for r in inputs.serving_requests(1e5, 400, seed=12)]
+        for t in warm:
+            t.submit()
+        for t in warm:
+            assert sv.poll(t, -1) == B.SV_OK
+        for rate in rates:
+            reqs = inputs.serving_requests(rate, n_requests)
+            odd = sum(odd_count(r.lo, r.hi) if r.kind != "points" else len(r.points) for r in reqs)
+            tickets = [sv.prepare_points(r.points) if r.kind == "points" else sv.prepare_range(r.lo, r.hi, list_cap=64)
+                       for r in reqs]
+            sv.reset_server_stats()
             t0 = time.perf_counter()
-            for r in reqs:
-                dt = t0 + r.t_arrival - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                if r.kind == "points":
-                    tickets.append(sv.submit_points(r.points))
-                else:
-                    tickets.append(sv.submit_range(r.lo, r.hi, list_cap=64))
+            lag = 0.0
+            for r, t in zip(reqs, tickets):
+                target = t0 + r.t_arrival
+                now = time.perf_counter()
+                if target - now > 3e-4:
+                    time.sleep(target - now - 2e-4)
+                while time.perf_counter() < target:
+                    pass
+                lag = max(lag, time.perf_counter() - target)
+                t.submit()
             for t in tickets:
                 st = sv.poll(t, -1)
                 assert st == B.SV_OK, B.sv_strerror(st)
             t1 = time.perf_counter()
             s = sv.server_stats()
-            out.append({"rate_per_s": rate, "requests": count, "odd_n": odd,
+            out.append({"rate_per_s": rate, "requests": n_requests, "odd_n": odd,
                         "value": odd / (t1 - t0), "unit": UNIT,
                         "offered": odd / max(reqs[-1].t_arrival, 1e-9),
-                        "p50_us": s.p50_us, "p99_us": s.p99_us, "launches": s.launches})
+                        "p50_us": s.p50_us, "p99_us": s.p99_us, "launches": s.launches,
+                        "max_submit_lag_us": lag * 1e6, "peak_mem_in_flight": s.peak_mem_in_flight})
     best = max(o["value"] for o in out)
-    return {"workload": "Poisson arrivals, seed 11: 70% ranges 2^12..2^16, 20% ranges 2^24..2^30, "
-                        "10% batches of 1..1024 points in [3, 2^50)",
-            "rates": out, "best_value": best, "unit": UNIT}
+    res = {"workload": "Poisson arrivals, seed 11: 70% ranges 2^12..2^16, 20% ranges 2^24..2^30, "
+                       "10% batches of 1..1024 points in [3, 2^50)",
+           "rates": out, "best_value": best, "unit": UNIT}
+    if batched:
+        res["best_vs_batched"] = best / batched["value"]
+    # the knee: the first rate whose throughput falls below 90% of what was offered
+    for o in out:
+        if o["value"] < 0.9 * o["offered"]:
+            res["knee_rate_per_s"] = o["rate_per_s"]
+            break
+    return res
 
 
 def measured_peaks() -> dict:
@@ -437,9 +516,11 @@ def main() -> int:
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-requests", type=int, default=4096)
-    ap.add_argument("--serve-seconds", type=float, default=1.5)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rates", default="1e2,1e3,1e4,1e5,3e5,1e6")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -594,6 +675,8 @@ def main() -> int:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], o = cpu_baseline(lo, hi, args.cpu_seconds, hi - lo)
         line["parity"] = parity_check(v, o)
+    if rank == 0 and world == 1 and not args.no_c3 and args.workload != "C3" and not args.range:
+        line["plain_C3"] = bench_range("C3", stream, flush, min(args.steps, 20), pk, knobs)
     if rank == 0 and world == 1 and not args.no_plain:
         fused = {"hist": res.hist, "first_n": res.first_n, "list_len": res.list_len, "list_n": res.list_n,
                  "ms": total_ms / args.steps}
@@ -601,7 +684,8 @@ def main() -> int:
     if rank == 0 and world == 1 and not args.no_batch:
         line["batched"] = bench_batch(v, stream, flush, args.batch_requests, tune=not args.no_tune)
     if rank == 0 and world == 1 and not args.no_serve:
-        line["served"] = bench_serving(stream, args.serve_seconds, line.get("batched"))
+        line["served"] = bench_serving(stream, args.serve_requests, [float(x) for x in args.serve_rates.split(",")],
+                                       line.get("batched"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

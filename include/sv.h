@@ -141,6 +141,9 @@ typedef struct sv_server_stats {
     uint64_t in_flight;       /* requests admitted and not yet completed */
     uint64_t queued;          /* requests waiting for admission */
     double p50_us, p99_us;    /* over completed requests since start */
+    uint64_t peak_mem_in_flight; /* largest device memory (the admission estimate) of the launches in
+                                    flight at one time; at most device_mem_budget unless a single
+                                    launch alone needs more */
 } sv_server_stats;
 
 /* Human-readable name of a status (static string, never NULL). */
@@ -287,7 +290,11 @@ sv_status sv_autotune_batch(sv_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
  * (continuous batching: requests that arrive while others are on the GPU are
  * packed into the next launches as device memory and launch slots free up;
  * long ranges are split so that they do not block short ones).  *ticket
- * identifies it.  SV_ENOMEM: the request alone exceeds the memory budget.
+ * identifies it.  Admission is by device memory: the launches in flight stay
+ * within sv_config.device_mem_budget, and a request waits until its next unit
+ * of work fits.  SV_ENOMEM: even the request's smallest unit of work (its
+ * first chunk of at most 2^30 integers, or one launch's points) exceeds the
+ * budget, or the queue is full; nothing is queued then.
  */
 sv_status sv_submit(sv_ctx *ctx, const sv_request *req, uint64_t *ticket);
 
@@ -301,8 +308,13 @@ sv_status sv_poll(sv_ctx *ctx, uint64_t ticket, int64_t timeout_us);
  * completes normally).  SV_OK if cancelled, SV_EAGAIN if already running. */
 sv_status sv_cancel(sv_ctx *ctx, uint64_t ticket);
 
-/* Serving counters since the server started (first sv_submit). */
+/* Serving counters since the server started (first sv_submit) or since the
+ * last sv_server_stats_reset. */
 sv_status sv_server_stats_get(sv_ctx *ctx, sv_server_stats *out);
+
+/* Restarts the serving counters and latency samples (requests in flight are
+ * not affected; their completions count in the new period). */
+sv_status sv_server_stats_reset(sv_ctx *ctx);
 
 /* Replace the tuning knobs (same rules as sv_create; the stream is kept). */
 sv_status sv_set_config(sv_ctx *ctx, const sv_config *cfg);
@@ -377,6 +389,16 @@ typedef struct sv_peaks {
  * buffer; changes no device setting.  Errors: SV_EINVAL, SV_ENOMEM, SV_ECUDA.
  */
 sv_status sv_measure_peaks(sv_ctx *ctx, sv_peaks *out);
+
+/*
+ * Test hook for the failure paths: the next `count` device or pinned-host
+ * buffer allocations the library makes (in any context of the process) fail
+ * as if memory were exhausted; the calls that needed them return SV_ENOMEM
+ * (a served request completes with SV_ENOMEM) and the library stays usable.
+ * count = 0 clears the hook.  No GPU operation is affected: the failure is
+ * made on the host, before the allocation call.
+ */
+sv_status sv_inject_alloc_failures(sv_ctx *ctx, uint32_t count);
 
 /* Number of kernels this context has launched so far. */
 uint64_t sv_kernel_launches(const sv_ctx *ctx);

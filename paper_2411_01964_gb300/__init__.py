@@ -225,9 +225,11 @@ class Verifier:
 
 
 class Ticket:
-    """A submitted serving request; keeps its buffers alive until it is polled."""
+    """A serving request and its buffers (kept alive until it is polled).
+    Submitted on construction unless submit=False; then submit() sends it."""
 
-    def __init__(self, v: "Verifier", kind: int, lo=0, hi=0, points=None, list_cap=4096, fail_cap=64):
+    def __init__(self, v: "Verifier", kind: int, lo=0, hi=0, points=None, list_cap=4096, fail_cap=64,
+                 submit: bool = True):
         self.kind = kind
         self.req = B.sv_request()
         self.req.kind = kind
@@ -244,9 +246,15 @@ class Ticket:
             self.req.points = self.points.ctypes.data_as(B.P(B.u64))
             self.req.n_points = len(self.points)
             self.req.out_k = self.out_k.ctypes.data_as(B.P(B.u8))
-        st, self.id = B.sv_submit(v.ctx, self.req)
-        B.check(st, "sv_submit")
+        self.ctx = v.ctx
+        self.id = None
         self.status = None
+        if submit:
+            self.submit()
+
+    def submit(self) -> None:
+        st, self.id = B.sv_submit(self.ctx, self.req)
+        B.check(st, "sv_submit")
 
     def result(self):
         if self.kind == B.SV_REQ_RANGE:
@@ -274,11 +282,24 @@ def _serving_methods():
     def server_stats(self) -> B.sv_server_stats:
         return B.sv_server_stats_get(self.ctx)
 
+    def reset_server_stats(self) -> None:
+        B.sv_server_stats_reset(self.ctx)
+
+    def prepare_range(self, lo: int, hi: int, *, list_cap: int = 4096, fail_cap: int = 64) -> Ticket:
+        """A range request with its buffers, not yet submitted (Ticket.submit)."""
+        return Ticket(self, B.SV_REQ_RANGE, lo=lo, hi=hi, list_cap=list_cap, fail_cap=fail_cap, submit=False)
+
+    def prepare_points(self, points) -> Ticket:
+        return Ticket(self, B.SV_REQ_POINTS, points=points, submit=False)
+
     Verifier.submit_range = submit_range
     Verifier.submit_points = submit_points
     Verifier.poll = poll
     Verifier.cancel = cancel
     Verifier.server_stats = server_stats
+    Verifier.reset_server_stats = reset_server_stats
+    Verifier.prepare_range = prepare_range
+    Verifier.prepare_points = prepare_points
 
 
 _serving_methods()

@@ -47,7 +47,7 @@ class sv_request(ctypes.Structure):
 class sv_server_stats(ctypes.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("cancelled", u64), ("refused", u64),
                 ("odd_n_done", u64), ("launches", u64), ("in_flight", u64), ("queued", u64),
-                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double)]
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("peak_mem_in_flight", u64)]
 
 
 class sv_peaks(ctypes.Structure):
@@ -87,9 +87,11 @@ _SIGS = {
     "sv_poll": (ctypes.c_int, [_CTX, u64, ctypes.c_int64]),
     "sv_cancel": (ctypes.c_int, [_CTX, u64]),
     "sv_server_stats_get": (ctypes.c_int, [_CTX, P(sv_server_stats)]),
+    "sv_server_stats_reset": (ctypes.c_int, [_CTX]),
     "sv_last_transfer": (ctypes.c_int, [_CTX, P(u64), P(u64)]),
     "sv_kernel_launches": (u64, [_CTX]),
     "sv_measure_peaks": (ctypes.c_int, [_CTX, P(sv_peaks)]),
+    "sv_inject_alloc_failures": (ctypes.c_int, [_CTX, u32]),
     "sv_kernel_timing": (ctypes.c_int, [_CTX, ctypes.c_int]),
     "sv_kernel_time": (ctypes.c_int, [_CTX, ctypes.c_int, P(ctypes.c_double), P(u64)]),
 }
@@ -279,6 +281,10 @@ def sv_server_stats_get(ctx) -> sv_server_stats:
     return s
 
 
+def sv_server_stats_reset(ctx) -> None:
+    check(load().sv_server_stats_reset(ctx), "sv_server_stats_reset")
+
+
 def sv_last_transfer(ctx) -> tuple[int, int]:
     a, b = u64(), u64()
     check(load().sv_last_transfer(ctx, ctypes.byref(a), ctypes.byref(b)), "sv_last_transfer")
@@ -317,3 +323,8 @@ def sv_measure_peaks(ctx) -> dict:
     pk = sv_peaks()
     check(load().sv_measure_peaks(ctx, ctypes.byref(pk)), "sv_measure_peaks")
     return {name: getattr(pk, name) for name, _ in sv_peaks._fields_ if name != "reserved"}
+
+
+def sv_inject_alloc_failures(ctx, count: int) -> None:
+    """Test hook: the next `count` buffer allocations of the library fail."""
+    check(load().sv_inject_alloc_failures(ctx, count), "sv_inject_alloc_failures")

@@ -17,6 +17,8 @@ using namespace sv;
 
 namespace sv {
 
+std::atomic<uint32_t> g_inject_alloc_failures{0};
+
 void Workspace::release_all() {
   if (gexec) cudaGraphExecDestroy(gexec);
   gexec = nullptr;
@@ -1402,6 +1404,12 @@ sv_status sv_last_transfer(const sv_ctx *c, uint64_t *h2d, uint64_t *d2h) {
 
 uint64_t sv_kernel_launches(const sv_ctx *c) { return c ? c->launches.load() : 0; }
 
+sv_status sv_inject_alloc_failures(sv_ctx *c, uint32_t count) {
+  if (!c) return SV_EINVAL;
+  g_inject_alloc_failures.store(count);
+  return SV_OK;
+}
+
 sv_status sv_kernel_timing(sv_ctx *c, int enable) {
   if (!c) return SV_EINVAL;
   SV_ON_DEVICE(c);
@@ -1648,6 +1656,12 @@ sv_status sv_cancel(sv_ctx *c, uint64_t ticket) {
   if (!c) return SV_EINVAL;
   if (!c->server) return SV_ENOTFOUND;
   return server_cancel(c->server, ticket);
+}
+
+sv_status sv_server_stats_reset(sv_ctx *c) {
+  if (!c) return SV_EINVAL;
+  if (c->server) server_reset_stats(c->server);
+  return SV_OK;
 }
 
 sv_status sv_server_stats_get(sv_ctx *c, sv_server_stats *out) {

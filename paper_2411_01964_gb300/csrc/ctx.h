@@ -15,6 +15,16 @@ namespace sv {
 
 constexpr int kPiBlockLog2 = 12;  // block size of the host prime-count index
 
+// Allocations still to fail on purpose (sv_inject_alloc_failures); takes one
+// if any is left.
+extern std::atomic<uint32_t> g_inject_alloc_failures;
+inline bool take_injected_failure() {
+  uint32_t n = g_inject_alloc_failures.load();
+  while (n > 0 && !g_inject_alloc_failures.compare_exchange_weak(n, n - 1)) {
+  }
+  return n > 0;
+}
+
 // Growable device / pinned-host buffer (grows geometrically, never shrinks).
 template <class T, bool PINNED>
 struct Buf {
@@ -25,6 +35,7 @@ struct Buf {
     size_t c = cap ? cap : 1;
     while (c < n) c *= 2;
     release();
+    if (take_injected_failure()) return cudaErrorMemoryAllocation;
     cudaError_t e = PINNED ? cudaMallocHost((void **)&p, c * sizeof(T)) : cudaMalloc((void **)&p, c * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
@@ -216,4 +227,5 @@ sv_status server_submit(Server *s, const sv_request *req, uint64_t *ticket);
 sv_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us);
 sv_status server_cancel(Server *s, uint64_t ticket);
 sv_status server_stats(Server *s, sv_server_stats *out);
+void server_reset_stats(Server *s);
 }  // namespace sv

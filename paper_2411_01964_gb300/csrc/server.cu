@@ -81,6 +81,16 @@ uint64_t chunk_list_cap(uint64_t n_odd, uint32_t T, uint64_t caller_cap) {
   return list_cap_estimate(n_odd, T, caller_cap);
 }
 
+// Device bytes a launch of `items` range chunks with `tiles` tiles in all,
+// `list` list entries and `points` point queries holds: tile buckets
+// (bucket_cap entries per tile, 1024 before the first launch sized them),
+// the per-tile list staging, lists, points, descriptors and result slots,
+// and 1 MiB of headers and straggler queue.
+uint64_t launch_mem(uint64_t tiles, uint64_t list, uint64_t points, uint64_t items, uint32_t bucket_cap) {
+  return tiles * 4ull * (bucket_cap ? bucket_cap + 1 : 1024) + tiles * (9ull * kStageCap + 4) + list * 9 +
+         points * 17 + (items + 1) * (sizeof(ReqDesc) + sizeof(ResultSlot)) + (1u << 20);
+}
+
 }  // namespace
 
 class Server {
@@ -135,9 +145,22 @@ class Server {
     } else {
       return SV_EINVAL;
     }
+    // admission: a request whose smallest unit of work (its first chunk, or
+    // one launch's worth of its points) does not fit the device memory budget
+    // could never run, and is refused
+    uint64_t unit_mem;
+    if (req->kind == SV_REQ_RANGE) {
+      const uint64_t len = req->hi > req->lo ? req->hi - req->lo : 0;
+      const uint64_t n = range_odd_count(req->lo, req->lo + (len < kChunkLen ? len : kChunkLen));
+      const uint64_t tile_odd = 1ull << c_->cfg.tile_log2;
+      unit_mem = launch_mem((n + tile_odd - 1) / tile_odd + 1,
+                            chunk_list_cap(n, c_->cfg.record_k_threshold, req->result->list_cap), 0, 1, 0);
+    } else {
+      unit_mem = launch_mem(0, 0, std::min<uint64_t>(req->n_points, kMaxPointsPerLaunch), 0, 0);
+    }
     std::lock_guard<std::mutex> lk(mu_);
     if (stop_) return SV_ECANCELLED;
-    if (queue_.size() >= kMaxQueued) {
+    if (queue_.size() >= kMaxQueued || unit_mem > c_->cfg.device_mem_budget) {
       ++refused_;
       return SV_ENOMEM;
     }
@@ -201,6 +224,13 @@ class Server {
     return SV_OK;
   }
 
+  void reset_stats() {
+    std::lock_guard<std::mutex> lk(mu_);
+    submitted_ = completed_ = cancelled_ = refused_ = odd_done_ = launches_ = 0;
+    peak_mem_ = 0;
+    lat_us_.clear();
+  }
+
   sv_status stats(sv_server_stats *o) {
     std::lock_guard<std::mutex> lk(mu_);
     std::memset(o, 0, sizeof(*o));
@@ -215,6 +245,7 @@ class Server {
     for (auto &kv : reqs_)
       if (kv.second.state == Request::kRunning) ++inflight;
     o->in_flight = inflight;
+    o->peak_mem_in_flight = peak_mem_;
     if (!lat_us_.empty()) {
       std::vector<double> v = lat_us_;
       const size_t i50 = v.size() / 2, i99 = std::min(v.size() - 1, (v.size() * 99) / 100);
@@ -245,10 +276,13 @@ class Server {
     const uint32_t T = c_->cfg.record_k_threshold;
     const uint64_t budget = c_->cfg.device_mem_budget;
     const uint64_t in_flight = mem_in_flight();
-    auto launch_mem = [&](uint64_t t, uint64_t l, uint64_t np) {
-      return t * 4ull * (s.ws.bucket_cap ? s.ws.bucket_cap + 1 : 1024) + t * (9ull * kStageCap + 4) + l * 9 + np * 17 +
-             (uint64_t)(s.items.size() + 1) * (sizeof(ReqDesc) + sizeof(ResultSlot)) + (1u << 20);
+    auto mem = [&](uint64_t t, uint64_t l, uint64_t np, uint64_t items) {
+      return launch_mem(t, l, np, items, s.ws.bucket_cap);
     };
+    // the budget holds for all launches in flight; the first unit of a
+    // launch may exceed it only when nothing else is in flight (it fits the
+    // budget alone: submit checked that)
+    auto over = [&](uint64_t m) { return in_flight + m > budget && (!s.items.empty() || s.npoints || in_flight); };
     for (auto it = queue_.begin(); it != queue_.end();) {
       Request &r = reqs_[*it];
       if (r.r.kind == SV_REQ_RANGE) {
@@ -258,7 +292,7 @@ class Server {
           const uint64_t n = range_odd_count(clo, chi);
           const uint64_t lc = chunk_list_cap(n, T, r.r.result->list_cap);
           const uint64_t t = (n + tile_odd - 1) / tile_odd + 1;
-          if (in_flight + launch_mem(tiles + t, listb + lc, s.npoints) > budget && !s.items.empty()) break;
+          if (over(mem(tiles + t, listb + lc, s.npoints, s.items.size() + 1))) break;
           RangeSpec sp;
           sp.lo = clo;
           sp.hi = chi;
@@ -284,6 +318,7 @@ class Server {
         const uint64_t room = kMaxPointsPerLaunch - s.npoints;
         if (room == 0) break;
         const uint64_t cnt = std::min<uint64_t>(room, r.r.n_points - r.next_point);
+        if (over(mem(tiles, listb, s.npoints + cnt, s.items.size()))) break;
         std::memcpy(s.ws.h_points.p + s.npoints, r.r.points + r.next_point, 8 * cnt);
         s.pitems.push_back({r.ticket, r.next_point, cnt, s.npoints});
         s.npoints += cnt;
@@ -298,8 +333,10 @@ class Server {
         break;
       }
     }
-    s.mem = launch_mem(tiles, listb, s.npoints);
-    return !s.items.empty() || s.npoints;
+    s.mem = mem(tiles, listb, s.npoints, s.items.size());
+    const bool any = !s.items.empty() || s.npoints;
+    if (any) peak_mem_ = std::max(peak_mem_, in_flight + s.mem);
+    return any;
   }
 
   // Enqueues slot s's launch (mu_ not held).
@@ -484,6 +521,7 @@ class Server {
   Slot slots_[kSlots];
   std::thread th_;
   uint64_t submitted_ = 0, completed_ = 0, cancelled_ = 0, refused_ = 0, odd_done_ = 0, launches_ = 0;
+  uint64_t peak_mem_ = 0;  // largest device memory of the launches in flight at once (estimated)
   std::vector<double> lat_us_;
 };
 
@@ -502,5 +540,6 @@ sv_status server_submit(Server *s, const sv_request *req, uint64_t *ticket) { re
 sv_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us) { return s->poll(ticket, timeout_us); }
 sv_status server_cancel(Server *s, uint64_t ticket) { return s->cancel(ticket); }
 sv_status server_stats(Server *s, sv_server_stats *out) { return s->stats(out); }
+void server_reset_stats(Server *s) { s->reset_stats(); }
 
 }  // namespace sv

@@ -75,3 +75,70 @@ def test_empty_and_invalid_requests():
         assert v.poll(t, -1) == B.SV_OK
         with pytest.raises(B.SvError):
             v.submit_range(1 << 42, (1 << 42) + 100)  # beyond the prime table
+
+
+# ---- admission by device memory and failure paths (all made on the host) ----
+
+def test_budget_refuses_what_can_never_fit():
+    with Verifier(max_hi=1 << 46, device_mem_budget=1 << 20) as v:
+        with pytest.raises(B.SvError) as e:
+            v.submit_range((1 << 45) + 1, (1 << 45) + (1 << 20))
+        assert e.value.status == B.SV_ENOMEM
+        with pytest.raises(B.SvError) as e:
+            v.submit_points([3, 5, 7])
+        assert e.value.status == B.SV_ENOMEM
+        assert v.server_stats().refused == 2
+
+
+def test_budget_queues_and_holds(orc):
+    budget = 14 << 20  # about two 2^30-integer chunks in flight at once
+    lo0 = (1 << 44) + 1
+    ranges = [(lo0 + i * (1 << 31), lo0 + i * (1 << 31) + (1 << 30) + 2 * i) for i in range(8)]
+    with Verifier(max_hi=1 << 46, device_mem_budget=budget) as v:
+        ts = [v.submit_range(a, b, list_cap=1 << 14) for a, b in ranges]
+        for t in ts:
+            assert v.poll(t, -1) == B.SV_OK
+        st = v.server_stats()
+        assert st.completed == len(ranges) and st.refused == 0
+        assert 0 < st.peak_mem_in_flight <= budget
+        for (a, b), t in zip(ranges, ts):
+            alone = v.verify_range(a, b, list_cap=1 << 14)
+            got = t.result()
+            assert got.hist == alone.hist and got.first_n == alone.first_n
+            assert np.array_equal(got.list_n, alone.list_n)
+
+
+def test_poll_with_finite_timeout():
+    lo, hi = (1 << 50) - (1 << 36), 1 << 50  # 2^35 odd n: milliseconds of work
+    with Verifier(max_hi=(1 << 50) + 1) as v:
+        t = v.submit_range(lo, hi)
+        assert v.poll(t, 0) == B.SV_EAGAIN
+        assert v.poll(t, 100) == B.SV_EAGAIN
+        assert v.poll(t, -1) == B.SV_OK
+        assert sum(t.result().hist) == (hi - lo) // 2
+
+
+def test_injected_allocation_failure_is_a_status(orc):
+    lo, hi = (1 << 44) + 1, (1 << 44) + (1 << 30)
+    try:
+        with Verifier(max_hi=1 << 46) as v:
+            t = v.submit_range((1 << 44) + 1, (1 << 44) + (1 << 16))  # warms one slot, small buffers
+            assert v.poll(t, -1) == B.SV_OK
+            B.sv_inject_alloc_failures(v.ctx, 1)  # the larger request's buffers must grow: that fails
+            t = v.submit_range(lo, hi)
+            assert v.poll(t, -1) == B.SV_ENOMEM
+            B.sv_inject_alloc_failures(v.ctx, 0)
+            t = v.submit_range(lo, hi)                                   # the server serves on
+            assert v.poll(t, -1) == B.SV_OK
+            o = orc.verify_range(lo, hi)
+            assert t.result().hist == o.hist and np.array_equal(t.result().list_n, o.list_n)
+        with Verifier(max_hi=1 << 46) as v:                              # the blocking path
+            B.sv_inject_alloc_failures(v.ctx, 1)
+            with pytest.raises(B.SvError) as e:
+                v.verify_range(lo, hi)
+            assert e.value.status == B.SV_ENOMEM
+            B.sv_inject_alloc_failures(v.ctx, 0)
+            assert v.verify_range(lo, hi).hist == orc.verify_range(lo, hi).hist
+    finally:
+        from paper_2411_01964_gb300 import binding
+        binding.load().sv_inject_alloc_failures(binding._CTX(1), 0)
