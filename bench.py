@@ -17,6 +17,8 @@ of the same workload.
 from __future__ import annotations
 
 import argparse
+import bisect
+import ctypes
 import json
 import math
 import os
@@ -359,10 +361,12 @@ def bench_plain(v, stream, flush, lo: int, hi: int, steps: int, fused: dict, hbm
 def bench_serving(stream, n_requests: int, rates, batched: dict | None) -> dict:
     """Config 5: open-loop Poisson arrivals (seed 11) of the serving mix at each
     rate, n_requests each.  Every request's structures and buffers are made
-    before the run, so the submitting thread keeps up with the arrival times
-    (it sleeps until shortly before an arrival, then spins).  Latency is the
+    before the run, so the submitting thread keeps up with the arrival times:
+    it sleeps until shortly before the next arrival, spins, and submits every
+    request that has arrived by then in one sv_submit_many call.  Latency is the
     server's own, from submission to completion; throughput is the odd n of
     all requests over the time from the first arrival to the last completion."""
+    import numpy as np
     from paper_2411_01964_gb300 import Verifier, B
     out = []
     with Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream) as sv:
@@ -378,18 +382,34 @@ def bench_serving(stream, n_requests: int, rates, batched: dict | None) -> dict:
             odd = sum(odd_count(r.lo, r.hi) if r.kind != "points" else len(r.points) for r in reqs)
             tickets = [sv.prepare_points(r.points) if r.kind == "points" else sv.prepare_range(r.lo, r.hi, list_cap=64)
                        for r in reqs]
+            # every request in one array: a burst is a slice of it, submitted by one call
+            arr = (B.sv_request * len(tickets))()
+            for i, t in enumerate(tickets):
+                arr[i] = t.req
+            ids = np.zeros(len(tickets), dtype=np.uint64)
+            sts = np.zeros(len(tickets), dtype=np.int32)
+            size = ctypes.sizeof(B.sv_request)
+            lib = B.load()
+            arrivals = [r.t_arrival for r in reqs]
             sv.reset_server_stats()
             t0 = time.perf_counter()
             lag = 0.0
-            for r, t in zip(reqs, tickets):
-                target = t0 + r.t_arrival
-                now = time.perf_counter()
-                if target - now > 3e-4:
-                    time.sleep(target - now - 2e-4)
-                while time.perf_counter() < target:
-                    pass
-                lag = max(lag, time.perf_counter() - target)
-                t.submit()
+            i, n_req = 0, len(tickets)
+            while i < n_req:
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:  # wait for the next arrival: sleep, then spin
+                    if arrivals[i] - now > 3e-4:
+                        time.sleep(arrivals[i] - now - 2e-4)
+                    continue
+                j = bisect.bisect_right(arrivals, now, i)
+                lag = max(lag, now - arrivals[i])
+                lib.sv_submit_many(sv.ctx, ctypes.cast(ctypes.addressof(arr) + i * size, ctypes.POINTER(B.sv_request)),
+                                   j - i, ids[i:].ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                   sts[i:].ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+                i = j
+            assert not sts.any(), "a serving request was refused"
+            for t, tid in zip(tickets, ids):
+                t.id = int(tid)
             for t in tickets:
                 st = sv.poll(t, -1)
                 assert st == B.SV_OK, B.sv_strerror(st)

@@ -298,6 +298,15 @@ sv_status sv_autotune_batch(sv_ctx *ctx, const uint64_t *lo, const uint64_t *hi,
  */
 sv_status sv_submit(sv_ctx *ctx, const sv_request *req, uint64_t *ticket);
 
+/*
+ * Several requests at once (a burst from one client): each is checked and
+ * queued as by sv_submit, all under one lock.  status[i] receives request i's
+ * outcome and tickets[i] its ticket where status[i] is SV_OK; the call returns
+ * the first failing status, or SV_OK.  reqs, tickets and status are HOST
+ * arrays of `count` entries.
+ */
+sv_status sv_submit_many(sv_ctx *ctx, const sv_request *reqs, size_t count, uint64_t *tickets, sv_status *status);
+
 /* SV_OK when the request has finished (its result is written), SV_EAGAIN if
  * still pending after timeout_us microseconds (0 = do not wait, < 0 = wait
  * without limit), SV_ECANCELLED, SV_ENOTFOUND.  A finished ticket is

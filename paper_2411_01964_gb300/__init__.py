@@ -292,6 +292,21 @@ def _serving_methods():
     def prepare_points(self, points) -> Ticket:
         return Ticket(self, B.SV_REQ_POINTS, points=points, submit=False)
 
+    def submit_many(self, tickets) -> None:
+        """Submits prepared tickets as one burst (sv_submit_many)."""
+        n = len(tickets)
+        if n == 0:
+            return
+        arr = (B.sv_request * n)()
+        for i, t in enumerate(tickets):
+            arr[i] = t.req
+        ids = np.zeros(n, dtype=np.uint64)
+        st = np.zeros(n, dtype=np.int32)
+        B.sv_submit_many(self.ctx, arr, ids, st)
+        for i, t in enumerate(tickets):
+            B.check(int(st[i]), "sv_submit_many")
+            t.id = int(ids[i])
+
     Verifier.submit_range = submit_range
     Verifier.submit_points = submit_points
     Verifier.poll = poll
@@ -300,6 +315,7 @@ def _serving_methods():
     Verifier.reset_server_stats = reset_server_stats
     Verifier.prepare_range = prepare_range
     Verifier.prepare_points = prepare_points
+    Verifier.submit_many = submit_many
 
 
 _serving_methods()

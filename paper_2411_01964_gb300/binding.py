@@ -84,6 +84,7 @@ _SIGS = {
     "sv_autotune": (ctypes.c_int, [_CTX, u64, u64, P(sv_config)]),
     "sv_autotune_batch": (ctypes.c_int, [_CTX, P(u64), P(u64), ctypes.c_size_t, P(sv_config)]),
     "sv_submit": (ctypes.c_int, [_CTX, P(sv_request), P(u64)]),
+    "sv_submit_many": (ctypes.c_int, [_CTX, P(sv_request), ctypes.c_size_t, P(u64), P(ctypes.c_int)]),
     "sv_poll": (ctypes.c_int, [_CTX, u64, ctypes.c_int64]),
     "sv_cancel": (ctypes.c_int, [_CTX, u64]),
     "sv_server_stats_get": (ctypes.c_int, [_CTX, P(sv_server_stats)]),
@@ -265,6 +266,13 @@ def sv_submit(ctx, req: sv_request) -> tuple[int, int]:
     t = u64()
     st = load().sv_submit(ctx, ctypes.byref(req), ctypes.byref(t))
     return st, t.value
+
+
+def sv_submit_many(ctx, reqs, tickets, status) -> int:
+    """reqs: a ctypes array of sv_request; tickets (uint64) and status (int32)
+    numpy arrays of the same length."""
+    return load().sv_submit_many(ctx, reqs, len(tickets), tickets.ctypes.data_as(P(u64)),
+                                 status.ctypes.data_as(P(ctypes.c_int)))
 
 
 def sv_poll(ctx, ticket: int, timeout_us: int) -> int:

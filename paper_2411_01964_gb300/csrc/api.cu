@@ -1646,6 +1646,20 @@ sv_status sv_submit(sv_ctx *c, const sv_request *req, uint64_t *ticket) {
   return server_submit(c->server, req, ticket);
 }
 
+sv_status sv_submit_many(sv_ctx *c, const sv_request *reqs, size_t count, uint64_t *tickets, sv_status *status) {
+  sv_status s = check_ready(c);
+  if (s) return s;
+  if (count && (!reqs || !tickets || !status)) return SV_EINVAL;
+  if (count == 0) return SV_OK;
+  SV_ON_DEVICE(c);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!c->server) c->server = server_create(c);
+    if (!c->server) return SV_ENOMEM;
+  }
+  return server_submit_many(c->server, reqs, count, tickets, status);
+}
+
 sv_status sv_poll(sv_ctx *c, uint64_t ticket, int64_t timeout_us) {
   if (!c) return SV_EINVAL;
   if (!c->server) return SV_ENOTFOUND;

@@ -224,6 +224,7 @@ sv_status tile_smem_ready(sv_ctx *c);
 Server *server_create(sv_ctx *c);
 void server_destroy(Server *s);
 sv_status server_submit(Server *s, const sv_request *req, uint64_t *ticket);
+sv_status server_submit_many(Server *s, const sv_request *reqs, size_t count, uint64_t *tickets, sv_status *status);
 sv_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us);
 sv_status server_cancel(Server *s, uint64_t ticket);
 sv_status server_stats(Server *s, sv_server_stats *out);

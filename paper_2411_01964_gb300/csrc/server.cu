@@ -134,31 +134,30 @@ class Server {
     }
   }
 
-  sv_status submit(const sv_request *req, uint64_t *ticket) {
+  // Validates one request and estimates its smallest unit's device memory
+  // (mu_ not needed).
+  sv_status check(const sv_request *req, uint64_t *unit_mem) const {
     if (req->kind == SV_REQ_RANGE) {
       if (!req->result) return SV_EINVAL;
       if (req->hi > c_->max_hi || req->hi > (1ull << 62)) return SV_ERANGE;
+      const uint64_t len = req->hi > req->lo ? req->hi - req->lo : 0;
+      const uint64_t n = range_odd_count(req->lo, req->lo + (len < kChunkLen ? len : kChunkLen));
+      const uint64_t tile_odd = 1ull << c_->cfg.tile_log2;
+      *unit_mem = launch_mem((n + tile_odd - 1) / tile_odd + 1,
+                             chunk_list_cap(n, c_->cfg.record_k_threshold, req->result->list_cap), 0, 1, 0);
     } else if (req->kind == SV_REQ_POINTS) {
       if (req->n_points && (!req->points || !req->out_k)) return SV_EINVAL;
       for (uint64_t i = 0; i < req->n_points; ++i)
         if (req->points[i] > c_->max_hi) return SV_ERANGE;
+      *unit_mem = launch_mem(0, 0, std::min<uint64_t>(req->n_points, kMaxPointsPerLaunch), 0, 0);
     } else {
       return SV_EINVAL;
     }
-    // admission: a request whose smallest unit of work (its first chunk, or
-    // one launch's worth of its points) does not fit the device memory budget
-    // could never run, and is refused
-    uint64_t unit_mem;
-    if (req->kind == SV_REQ_RANGE) {
-      const uint64_t len = req->hi > req->lo ? req->hi - req->lo : 0;
-      const uint64_t n = range_odd_count(req->lo, req->lo + (len < kChunkLen ? len : kChunkLen));
-      const uint64_t tile_odd = 1ull << c_->cfg.tile_log2;
-      unit_mem = launch_mem((n + tile_odd - 1) / tile_odd + 1,
-                            chunk_list_cap(n, c_->cfg.record_k_threshold, req->result->list_cap), 0, 1, 0);
-    } else {
-      unit_mem = launch_mem(0, 0, std::min<uint64_t>(req->n_points, kMaxPointsPerLaunch), 0, 0);
-    }
-    std::lock_guard<std::mutex> lk(mu_);
+    return SV_OK;
+  }
+
+  // Queues a checked request (mu_ held).
+  sv_status enqueue_locked(const sv_request *req, uint64_t unit_mem, uint64_t *ticket) {
     if (stop_) return SV_ECANCELLED;
     if (queue_.size() >= kMaxQueued || unit_mem > c_->cfg.device_mem_budget) {
       ++refused_;
@@ -179,9 +178,34 @@ class Server {
       complete(r);
     } else {
       queue_.push_back(t);
-      cv_work_.notify_one();
     }
     return SV_OK;
+  }
+
+  // Several requests under one lock; status[i] per request, tickets[i] valid
+  // where status[i] is SV_OK.  Returns the first failing status (or SV_OK).
+  sv_status submit_many(const sv_request *reqs, size_t count, uint64_t *tickets, sv_status *status) {
+    std::vector<uint64_t> mem(count);
+    sv_status first = SV_OK;
+    for (size_t i = 0; i < count; ++i) {
+      status[i] = check(&reqs[i], &mem[i]);
+      if (status[i] && !first) first = status[i];
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      for (size_t i = 0; i < count; ++i) {
+        if (status[i]) continue;
+        status[i] = enqueue_locked(&reqs[i], mem[i], &tickets[i]);
+        if (status[i] && !first) first = status[i];
+      }
+    }
+    cv_work_.notify_one();
+    return first;
+  }
+
+  sv_status submit(const sv_request *req, uint64_t *ticket) {
+    sv_status st;
+    return submit_many(req, 1, ticket, &st);
   }
 
   sv_status poll(uint64_t ticket, int64_t timeout_us) {
@@ -537,6 +561,9 @@ Server *server_create(sv_ctx *c) {
 
 void server_destroy(Server *s) { delete s; }
 sv_status server_submit(Server *s, const sv_request *req, uint64_t *ticket) { return s->submit(req, ticket); }
+sv_status server_submit_many(Server *s, const sv_request *reqs, size_t count, uint64_t *tickets, sv_status *status) {
+  return s->submit_many(reqs, count, tickets, status);
+}
 sv_status server_poll(Server *s, uint64_t ticket, int64_t timeout_us) { return s->poll(ticket, timeout_us); }
 sv_status server_cancel(Server *s, uint64_t ticket) { return s->cancel(ticket); }
 sv_status server_stats(Server *s, sv_server_stats *out) { return s->stats(out); }

@@ -142,3 +142,27 @@ def test_injected_allocation_failure_is_a_status(orc):
     finally:
         from paper_2411_01964_gb300 import binding
         binding.load().sv_inject_alloc_failures(binding._CTX(1), 0)
+
+
+def test_burst_submission_equals_single(orc):
+    reqs = small_mix(96, seed=13)
+    with Verifier(max_hi=inputs.TABLE_MAX_HI) as v:
+        burst = [v.prepare_points(r.points) if r.kind == "points" else v.prepare_range(r.lo, r.hi, list_cap=4096)
+                 for r in reqs]
+        v.submit_many(burst[:50])
+        v.submit_many(burst[50:])
+        for t in burst:
+            assert v.poll(t, -1) == B.SV_OK
+        for r, t in zip(reqs, burst):
+            if r.kind == "points":
+                assert np.array_equal(t.result(), orc.min_k(r.points))
+            else:
+                alone = v.verify_range(r.lo, r.hi, list_cap=4096)
+                assert t.result().hist == alone.hist and np.array_equal(t.result().list_n, alone.list_n)
+        # a bad request in a burst fails alone; the others are queued
+        good = v.prepare_range((1 << 40) + 1, (1 << 40) + 1001)
+        bad = v.prepare_range(1 << 52, (1 << 52) + 10)  # beyond the prime table
+        with pytest.raises(B.SvError) as e:
+            v.submit_many([good, bad])
+        assert e.value.status == B.SV_ERANGE
+        assert good.id is not None and v.poll(good, -1) == B.SV_OK
