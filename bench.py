@@ -197,11 +197,13 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3, tune: bool = 
     c = v0.config
     v = Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream, tile_log2=c.tile_log2, threads=c.threads,
                  ctas_per_sm=c.ctas_per_sm, margin_log2=c.margin_log2, stamp_primes=c.stamp_primes)
+    import numpy as np
     reqs = inputs.batch_requests(7, n_requests)
-    los = [a for a, _ in reqs]
-    his = [b for _, b in reqs]
+    los = np.array([a for a, _ in reqs], dtype=np.uint64)  # the batch's input arrays, made before timing
+    his = np.array([b for _, b in reqs], dtype=np.uint64)
     n_odd = sum(odd_count(a, b) for a, b in reqs)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    host = []
 
     def time_batch():
         v.launch_batch(los, his)  # warm-up: captures the graph
@@ -210,7 +212,9 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3, tune: bool = 
         for _ in range(reps):
             flush.zero_()
             ev[0].record(stream)
+            t0 = time.perf_counter()
             v.launch_batch(los, his)
+            host.append(time.perf_counter() - t0)
             ev[1].record(stream)
             torch.cuda.synchronize()
             bt.append(ev[0].elapsed_time(ev[1]))
@@ -234,7 +238,8 @@ def bench_batch(v0, stream, flush, n_requests: int, reps: int = 3, tune: bool = 
            "odd_n": n_odd, "ms": ms_default, "value": n_odd / (ms_default / 1e3), "unit": UNIT,
            "config": cfg_default, "plain_ms": pt, "plain_value": n_odd / (pt / 1e3),
            "speedup_vs_plain": pt / ms_default, "graph": "one captured graph, replayed per batch",
-           "timed": "CUDA events around the launch call: host planning, descriptor upload and kernels"}
+           "timed": "CUDA events around the launch call: host planning, descriptor upload and kernels",
+           "host_ms_in_launch_call": 1e3 * min(host)}
     if tune:
         t0 = time.perf_counter()
         v.autotune_batch(los[::8], his[::8])
@@ -358,7 +363,7 @@ def bench_plain(v, stream, flush, lo: int, hi: int, steps: int, fused: dict, hbm
                                            "frac": r_gbs / hbm_gbs if hbm_gbs else None}}}
 
 
-def bench_serving(stream, n_requests: int, rates, batched: dict | None) -> dict:
+def bench_serving(stream, n_requests: int, rates, batched: dict | None, knobs: dict | None = None) -> dict:
     """Config 5: open-loop Poisson arrivals (seed 11) of the serving mix at each
     rate, n_requests each.  Every request's structures and buffers are made
     before the run, so the submitting thread keeps up with the arrival times:
@@ -369,7 +374,7 @@ def bench_serving(stream, n_requests: int, rates, batched: dict | None) -> dict:
     import numpy as np
     from paper_2411_01964_gb300 import Verifier, B
     out = []
-    with Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream) as sv:
+    with Verifier(max_hi=inputs.TABLE_MAX_HI, stream=stream.cuda_stream, **(knobs or {})) as sv:
         # warm-up: a short mix sizes every slot's buffers and captures its graphs
         warm = [sv.prepare_points(r.points) if r.kind == "points" else sv.prepare_range(r.lo, r.hi, list_cap=64)
                 for r in inputs.serving_requests(1e5, 400, seed=12)]
@@ -419,11 +424,13 @@ def bench_serving(stream, n_requests: int, rates, batched: dict | None) -> dict:
                         "value": odd / (t1 - t0), "unit": UNIT,
                         "offered": odd / max(reqs[-1].t_arrival, 1e-9),
                         "p50_us": s.p50_us, "p99_us": s.p99_us, "launches": s.launches,
-                        "max_submit_lag_us": lag * 1e6, "peak_mem_in_flight": s.peak_mem_in_flight})
+                        "max_submit_lag_us": lag * 1e6, "peak_mem_in_flight": s.peak_mem_in_flight,
+                        "loop_busy_frac": s.loop_busy_us / max(s.wall_us, 1e-9)})
+        sv_slots = sv.config.serve_slots
     best = max(o["value"] for o in out)
     res = {"workload": "Poisson arrivals, seed 11: 70% ranges 2^12..2^16, 20% ranges 2^24..2^30, "
                        "10% batches of 1..1024 points in [3, 2^50)",
-           "rates": out, "best_value": best, "unit": UNIT}
+           "rates": out, "best_value": best, "unit": UNIT, "serve_slots": sv_slots}
     if batched:
         res["best_vs_batched"] = best / batched["value"]
     # the knee: the first rate whose throughput falls below 90% of what was offered

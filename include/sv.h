@@ -93,6 +93,9 @@ typedef struct sv_config {
                                     buckets by enumerating the odd multipliers j of j p^2 in the range
                                     (cheap for many short ranges far up); smaller bucket primes take one
                                     Barrett reduction per range (10..31; 0 = 18) */
+    uint32_t serve_slots;        /* launches the serving loop keeps in flight, each on its own stream
+                                    with its own device workspace (1..8; 0 = 4) */
+    uint32_t reserved1;
 } sv_config;
 
 /*
@@ -144,6 +147,9 @@ typedef struct sv_server_stats {
     uint64_t peak_mem_in_flight; /* largest device memory (the admission estimate) of the launches in
                                     flight at one time; at most device_mem_budget unless a single
                                     launch alone needs more */
+    double wall_us;           /* time since the server started or the stats were reset */
+    double loop_busy_us;      /* of that, time the serving thread spent packing, launching and
+                                 collecting (the rest it waited for work or for the GPU) */
 } sv_server_stats;
 
 /* Human-readable name of a status (static string, never NULL). */

@@ -29,7 +29,8 @@ class sv_config(ctypes.Structure):
     _fields_ = [("tile_log2", u32), ("margin_log2", u32), ("threads", u32), ("large_prime_min", u32),
                 ("bucket_capacity", u32), ("record_k_threshold", u32), ("ctas_per_sm", u32),
                 ("stamp_primes", u32), ("list_capacity", u64), ("device_mem_budget", u64),
-                ("cuda_stream", ctypes.c_void_p), ("list_stage_capacity", u32), ("mult_prime_log2", u32)]
+                ("cuda_stream", ctypes.c_void_p), ("list_stage_capacity", u32), ("mult_prime_log2", u32),
+                ("serve_slots", u32), ("reserved1", u32)]
 
 
 class sv_range_result(ctypes.Structure):
@@ -47,7 +48,8 @@ class sv_request(ctypes.Structure):
 class sv_server_stats(ctypes.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("cancelled", u64), ("refused", u64),
                 ("odd_n_done", u64), ("launches", u64), ("in_flight", u64), ("queued", u64),
-                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("peak_mem_in_flight", u64)]
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("peak_mem_in_flight", u64),
+                ("wall_us", ctypes.c_double), ("loop_busy_us", ctypes.c_double)]
 
 
 class sv_peaks(ctypes.Structure):

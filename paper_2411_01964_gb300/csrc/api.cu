@@ -119,6 +119,8 @@ sv_status normalise_config(sv_ctx *c, sv_config *k) {
   if (c->smem_optin && smem + tile_static_smem() + 1024 > c->smem_optin) return SV_EINVAL;  // window + static
   if (k->large_prime_min == 0) k->large_prime_min = 1u << ((k->tile_log2 + 1) / 2);
   if (k->mult_prime_log2 == 0) k->mult_prime_log2 = kMultPrimeLog2;
+  if (k->serve_slots == 0) k->serve_slots = 4;
+  if (k->serve_slots > 8) return SV_EINVAL;
   if (k->mult_prime_log2 < 10 || k->mult_prime_log2 > 31) return SV_EINVAL;
   return SV_OK;
 }
@@ -211,7 +213,8 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   if (ws.h_hdr.ensure(1) != cudaSuccess) return SV_ENOMEM;
   uint64_t tiles = 0, list_total = 0, fail_total = 0;
   uint32_t max_primes = 0;
-  uint64_t j_max = 0;
+  uint64_t jhi_max = 0;  // the largest odd multiplier floor((2 jhi - 1) / p_hyb^2) grows with jhi
+  uint64_t hi_max = 0;   // and the largest prime count with hi
   const uint64_t ph2 = g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb;
   bool any_per_n = false;
   bool all_from_bitmap = n > 0;
@@ -238,9 +241,8 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
     d.n_tiles = (uint32_t)nt;
     d.tile_base = (uint32_t)tiles;
     tiles += nt;
-    d.n_primes = (s.hi > 1) ? primes_upto(c, host_isqrt(s.hi - 1)) : 0;
-    if (nt && d.n_primes > max_primes) max_primes = d.n_primes;
-    if (nt && ph2 && d.jhi) j_max = std::max<uint64_t>(j_max, (2 * d.jhi - 1) / ph2);
+    if (nt && s.hi > hi_max) hi_max = s.hi;  // n_primes itself is counted on the device (init kernel)
+    if (nt && d.jhi > jhi_max) jhi_max = d.jhi;
     d.per_n_k = s.d_per_n;
     any_per_n |= (s.d_per_n != nullptr);
     d.list_off = list_total;
@@ -256,6 +258,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
     all_from_bitmap &= (s.bitmap_in != nullptr);
     ws.h_reqs.p[r] = d;
   }
+  if (hi_max > 1) max_primes = primes_upto(c, host_isqrt(hi_max - 1));
   LaunchHeader h{};
   h.n_reqs = n;
   h.total_tiles = (uint32_t)tiles;
@@ -266,7 +269,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   ws.max_primes = max_primes;
   ws.list_total = list_total;
   ws.fail_total = fail_total;
-  ws.j_max = j_max;
+  ws.j_max = (ph2 && jhi_max) ? (2 * jhi_max - 1) / ph2 : 0;
   ws.any_per_n = any_per_n;
   ws.all_from_bitmap = all_from_bitmap;
   ws.ordered = !any_per_n && g.rec_t > 5 && !ws.force_general;
@@ -342,7 +345,7 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
   {
     KTimer kt(c, kKInit, st);
     SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, mode == 0 ? ws.stage_cnt.p : nullptr,
-                            ws.total_tiles, ws.reqs.p, g.mw, st));
+                            ws.total_tiles, ws.reqs.p, g.mw, c->d_p, c->n_primes, st));
     kt.done();
   }
   c->launches++;
@@ -472,7 +475,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
     // sized for the buffers (the kernel reads the launch's sizes from the header)
     if (!e) e = launch_init(ws.hdr.p, ws.slots.p, (uint32_t)std::min<size_t>(ws.slots.cap, 1u << 20), ws.bucket_count.p,
                             mode == 0 ? ws.stage_cnt.p : nullptr, (uint32_t)std::min<size_t>(ws.bucket_count.cap, 1u << 30),
-                            ws.reqs.p, g.mw, st);
+                            ws.reqs.p, g.mw, c->d_p, c->n_primes, st);
     if (!e && pt.n > g.i_large) {
       BucketArgs b{};
       b.pt = pt;

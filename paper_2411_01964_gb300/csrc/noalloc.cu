@@ -239,7 +239,8 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
       return SV_ECUDA;
     // the array keeps the previous call's contents: the counters, the result
     // slot and the bucket counts are cleared on the device first
-    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, d_req, g.mw, st) != cudaSuccess) return SV_ECUDA;
+    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, d_req, g.mw, c->d_p, c->n_primes, st) != cudaSuccess)
+      return SV_ECUDA;
     c->launches++;
     if (d.n_primes > g.i_large) {
       BucketArgs b{};

@@ -1,6 +1,6 @@
 // server.cu -- the serving loop behind sv_submit / sv_poll / sv_cancel.
 //
-// Continuous batching: a worker thread keeps up to kSlots launches in flight,
+// Continuous batching: a worker thread keeps up to serve_slots launches in flight,
 // each on its own stream with its own device workspace, so their kernels
 // overlap on the GPU.  Whenever a slot frees up, everything queued is packed
 // into the next launch: range requests are cut into chunks of at most
@@ -31,7 +31,7 @@ namespace sv {
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kSlots = 3;
+constexpr int kMaxSlots = 8;  // launch slots at most (sv_config.serve_slots)
 constexpr uint64_t kChunkLen = 1ull << 30;        // integers per range chunk
 constexpr uint64_t kMaxOddPerLaunch = 1ull << 32; // odd n per launch
 constexpr uint64_t kMaxPointsPerLaunch = 1ull << 16;
@@ -95,11 +95,12 @@ uint64_t launch_mem(uint64_t tiles, uint64_t list, uint64_t points, uint64_t ite
 
 class Server {
  public:
-  explicit Server(sv_ctx *c) : c_(c) {}
+  explicit Server(sv_ctx *c) : c_(c), n_slots_((int)std::min<uint32_t>(std::max<uint32_t>(c->cfg.serve_slots, 1), kMaxSlots)) {}
   ~Server() { shutdown(); }
 
   sv_status init() {
-    for (auto &s : slots_) {
+    for (int i = 0; i < n_slots_; ++i) {
+      Slot &s = slots_[i];
       if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess) return SV_ECUDA;
       if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) return SV_ECUDA;
       // staging for the points of one launch, sized once: fill() packs several
@@ -124,7 +125,8 @@ class Server {
       if (kv.second.state == Request::kQueued || kv.second.state == Request::kRunning)
         kv.second.state = Request::kCancelled;
     cv_done_.notify_all();
-    for (auto &s : slots_) {
+    for (int i = 0; i < n_slots_; ++i) {
+      Slot &s = slots_[i];
       if (s.st) cudaStreamSynchronize(s.st);
       s.ws.release_all();
       if (s.ev) cudaEventDestroy(s.ev);
@@ -253,6 +255,8 @@ class Server {
     submitted_ = completed_ = cancelled_ = refused_ = odd_done_ = launches_ = 0;
     peak_mem_ = 0;
     lat_us_.clear();
+    t_reset_ = Clock::now();
+    busy_us_ = 0.0;
   }
 
   sv_status stats(sv_server_stats *o) {
@@ -270,6 +274,8 @@ class Server {
       if (kv.second.state == Request::kRunning) ++inflight;
     o->in_flight = inflight;
     o->peak_mem_in_flight = peak_mem_;
+    o->wall_us = std::chrono::duration<double, std::micro>(Clock::now() - t_reset_).count();
+    o->loop_busy_us = busy_us_;
     if (!lat_us_.empty()) {
       std::vector<double> v = lat_us_;
       const size_t i50 = v.size() / 2, i99 = std::min(v.size() - 1, (v.size() * 99) / 100);
@@ -284,8 +290,8 @@ class Server {
  private:
   uint64_t mem_in_flight() const {
     uint64_t m = 0;
-    for (auto &s : slots_)
-      if (s.busy) m += s.mem;
+    for (int i = 0; i < n_slots_; ++i)
+      if (slots_[i].busy) m += slots_[i].mem;
     return m;
   }
 
@@ -498,19 +504,25 @@ class Server {
     std::unique_lock<std::mutex> lk(mu_);
     for (;;) {
       bool busy = false;
-      for (auto &s : slots_) {
+      for (int i = 0; i < n_slots_; ++i) {
+        Slot &s = slots_[i];
         if (!s.busy) continue;
         if (cudaEventQuery(s.ev) != cudaErrorNotReady) {
           lk.unlock();
+          const auto t0 = Clock::now();
           finish(s, SV_OK);
+          const auto t1 = Clock::now();
           lk.lock();
+          busy_us_ += std::chrono::duration<double, std::micro>(t1 - t0).count();
         } else {
           busy = true;
         }
       }
       if (!stop_) {
-        for (auto &s : slots_) {
+        for (int i = 0; i < n_slots_; ++i) {
+          Slot &s = slots_[i];
           if (s.busy || queue_.empty()) continue;
+          const auto t0 = Clock::now();
           if (!fill(s)) continue;
           s.busy = true;
           lk.unlock();
@@ -518,9 +530,12 @@ class Server {
           if (st) {
             finish(s, st);
             lk.lock();
+            busy_us_ += std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
             continue;
           }
+          const auto t1 = Clock::now();
           lk.lock();
+          busy_us_ += std::chrono::duration<double, std::micro>(t1 - t0).count();
           busy = true;
         }
       }
@@ -542,7 +557,10 @@ class Server {
   std::unordered_map<uint64_t, Request> reqs_;
   uint64_t next_ticket_ = 1;
   bool stop_ = false;
-  Slot slots_[kSlots];
+  Slot slots_[kMaxSlots];
+  int n_slots_ = 3;
+  Clock::time_point t_reset_ = Clock::now();
+  double busy_us_ = 0.0;  // the loop thread's time in fill / start / finish
   std::thread th_;
   uint64_t submitted_ = 0, completed_ = 0, cancelled_ = 0, refused_ = 0, odd_done_ = 0, launches_ = 0;
   uint64_t peak_mem_ = 0;  // largest device memory of the launches in flight at once (estimated)

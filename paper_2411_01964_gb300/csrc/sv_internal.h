@@ -57,7 +57,7 @@ struct ReqDesc {
   uint32_t n_tiles;     // tiles of this range
   uint32_t tile_base;   // global index of tile 0
   uint32_t slot;        // result slot
-  uint32_t n_primes;    // primes p with p^2 < hi (p <= isqrt(hi - 1))
+  uint32_t n_primes;    // primes p with p^2 < hi (p <= isqrt(hi - 1)); set by the init kernel
   uint8_t *per_n_k;     // optional device output, index (n - nlo) / 2
   uint64_t list_off, list_cap;  // this range's region of the list arena
   uint64_t fail_off, fail_cap;  // this range's region of the failure arena
@@ -188,7 +188,7 @@ struct CompactArgs {
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, ReqDesc *reqs, uint32_t mw,
-                        cudaStream_t st);
+                        const uint32_t *primes, uint32_t n_table, cudaStream_t st);
 cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st);
 // n_large_max, n_reqs: upper bounds of the launch's bucket primes and ranges;
 // j_max: the largest odd multiplier any range needs for the primes >= p_hyb.

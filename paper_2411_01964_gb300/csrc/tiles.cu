@@ -163,11 +163,13 @@ __device__ __forceinline__ void strike(uint32_t *win, uint32_t b) {
 
 // ---------------------------------------------------------------------------
 // init: zero the launch's counters, result slots, bucket and staged-list
-// counts; give each range the integer square roots of its bucket-fill
-// interval ends (ReqDesc::sq_lo, sq_hi) for the multiplier items.
+// counts; give each range its number of table primes p with p^2 < hi
+// (Algorithm 1's "primes 3 <= p < sqrt(end)", ReqDesc::n_primes) and the
+// integer square roots of its bucket-fill interval ends (ReqDesc::sq_lo,
+// sq_hi) for the multiplier items.
 // ---------------------------------------------------------------------------
 __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count, uint32_t *stage_cnt,
-                            ReqDesc *reqs, uint32_t mw) {
+                            ReqDesc *reqs, uint32_t mw, const uint32_t *primes, uint32_t n_table) {
   const uint32_t n_slots = hdr->n_reqs, n_tiles = hdr->total_tiles;
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gs = gridDim.x * blockDim.x;
@@ -177,6 +179,15 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
     const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);  // the fill's window bits [A, E = jhi)
     R.sq_lo = (uint32_t)isqrt_u64(2 * A);
     R.sq_hi = R.jhi ? (uint32_t)isqrt_u64(2 * R.jhi - 1) : 0u;
+    // the count of table primes p <= isqrt(hi - 1): the first index with p > x
+    const uint64_t x = R.hi > 1 ? isqrt_u64(R.hi - 1) : 0;
+    uint32_t lo = 0, hi = n_table;
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if ((uint64_t)primes[mid] <= x) lo = mid + 1;
+      else hi = mid;
+    }
+    R.n_primes = lo;
   }
   for (uint32_t i = gid; i < n_tiles; i += gs) {
     bucket_count[i] = 0;
@@ -199,13 +210,13 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
 
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, ReqDesc *reqs, uint32_t mw,
-                        cudaStream_t st) {
+                        const uint32_t *primes, uint32_t n_table, cudaStream_t st) {
   uint64_t work = (uint64_t)n_slots * kMaxK;
   if (n_tiles > work) work = n_tiles;
   uint32_t grid = (uint32_t)((work + 255) / 256);
   if (grid < 1) grid = 1;
   if (grid > 1024) grid = 1024;
-  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt, reqs, mw);
+  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt, reqs, mw, primes, n_table);
   return cudaGetLastError();
 }
 
