@@ -241,7 +241,16 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
     d.n_tiles = (uint32_t)nt;
     d.tile_base = (uint32_t)tiles;
     tiles += nt;
-    if (nt && s.hi > hi_max) hi_max = s.hi;  // n_primes itself is counted on the device (init kernel)
+    if (nt && s.hi > hi_max) hi_max = s.hi;
+    if (n <= kHostPlanMax) {  // few ranges: planned here; many: by the init kernel, in parallel
+      d.n_primes = s.hi > 1 ? primes_upto(c, host_isqrt(s.hi - 1)) : 0;
+      const int64_t ws = d.w0 - (int64_t)g.mw;
+      const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
+      d.sq_lo = (uint32_t)host_isqrt(2 * A);
+      d.sq_hi = d.jhi ? (uint32_t)host_isqrt(2 * d.jhi - 1) : 0u;
+    } else {
+      d.n_primes = kPlanOnDevice;
+    }
     if (nt && d.jhi > jhi_max) jhi_max = d.jhi;
     d.per_n_k = s.d_per_n;
     any_per_n |= (s.d_per_n != nullptr);

@@ -201,7 +201,13 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
   d.wend = (int64_t)((d.jhi + 31) >> 5);
   const uint64_t nwords = (d.jhi > d.jlo) ? (uint64_t)(d.wend - d.w0) : 0;
   const uint64_t nt = (nwords + g.tw - 1) / g.tw;
-  d.n_primes = hi > 1 ? primes_upto_of(c, host_isqrt(hi - 1)) : 0;
+  d.n_primes = hi > 1 ? primes_upto_of(c, host_isqrt(hi - 1)) : 0;  // planned here, as for a single range
+  {
+    const int64_t ws = d.w0 - (int64_t)g.mw;
+    const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
+    d.sq_lo = (uint32_t)host_isqrt(2 * A);
+    d.sq_hi = d.jhi ? (uint32_t)host_isqrt(2 * d.jhi - 1) : 0u;
+  }
   d.list_cap = kNaList;
   d.fail_cap = kNaFail;
 

@@ -14,6 +14,10 @@
 namespace sv {
 
 constexpr int kMaxK = 64;
+// ReqDesc::n_primes of a range whose prime count and interval roots the init
+// kernel computes (the host plans them itself for launches of few ranges)
+constexpr uint32_t kPlanOnDevice = 0xFFFFFFFFu;
+constexpr uint32_t kHostPlanMax = 32;  // ranges per launch the host plans itself
 constexpr uint8_t kFailK = 255;
 constexpr unsigned long long kNoN = ~0ull;
 
@@ -57,7 +61,8 @@ struct ReqDesc {
   uint32_t n_tiles;     // tiles of this range
   uint32_t tile_base;   // global index of tile 0
   uint32_t slot;        // result slot
-  uint32_t n_primes;    // primes p with p^2 < hi (p <= isqrt(hi - 1)); set by the init kernel
+  uint32_t n_primes;    // primes p with p^2 < hi (p <= isqrt(hi - 1)); kPlanOnDevice: the init kernel
+                        // counts them (and sets sq_lo, sq_hi), for launches of many ranges
   uint8_t *per_n_k;     // optional device output, index (n - nlo) / 2
   uint64_t list_off, list_cap;  // this range's region of the list arena
   uint64_t fail_off, fail_cap;  // this range's region of the failure arena

@@ -163,10 +163,11 @@ __device__ __forceinline__ void strike(uint32_t *win, uint32_t b) {
 
 // ---------------------------------------------------------------------------
 // init: zero the launch's counters, result slots, bucket and staged-list
-// counts; give each range its number of table primes p with p^2 < hi
-// (Algorithm 1's "primes 3 <= p < sqrt(end)", ReqDesc::n_primes) and the
-// integer square roots of its bucket-fill interval ends (ReqDesc::sq_lo,
-// sq_hi) for the multiplier items.
+// counts; give each range of a large launch its number of table primes p
+// with p^2 < hi (Algorithm 1's "primes 3 <= p < sqrt(end)",
+// ReqDesc::n_primes) and the integer square roots of its bucket-fill interval
+// ends (ReqDesc::sq_lo, sq_hi) for the multiplier items; the host plans these
+// itself for launches of few ranges.
 // ---------------------------------------------------------------------------
 __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count, uint32_t *stage_cnt,
                             ReqDesc *reqs, uint32_t mw, const uint32_t *primes, uint32_t n_table) {
@@ -175,6 +176,7 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
   const uint32_t gs = gridDim.x * blockDim.x;
   for (uint32_t r = gid; r < n_slots; r += gs) {
     ReqDesc &R = reqs[r];
+    if (R.n_primes != kPlanOnDevice) continue;  // planned on the host
     const int64_t ws = R.w0 - (int64_t)mw;
     const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);  // the fill's window bits [A, E = jhi)
     R.sq_lo = (uint32_t)isqrt_u64(2 * A);
