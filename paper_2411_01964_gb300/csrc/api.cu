@@ -182,6 +182,9 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   return g;
 }
 
+// p_hyb^2: multiples j p^2 with p >= p_hyb are enumerated by j (0: none)
+uint64_t p_hyb_sq(const Geometry &g) { return g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb; }
+
 PrimeTab prime_tab(const sv_ctx *c) {
   PrimeTab pt{};
   pt.p = c->d_p;
@@ -248,6 +251,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
       const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
       d.sq_lo = (uint32_t)host_isqrt(2 * A);
       d.sq_hi = d.jhi ? (uint32_t)host_isqrt(2 * d.jhi - 1) : 0u;
+      d.j_max = (ph2 && d.jhi) ? (2 * d.jhi - 1) / ph2 : 0;
     } else {
       d.n_primes = kPlanOnDevice;
     }
@@ -269,6 +273,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   }
   if (hi_max > 1) max_primes = primes_upto(c, host_isqrt(hi_max - 1));
   LaunchHeader h{};
+  h.j_max = (ph2 && jhi_max) ? (2 * jhi_max - 1) / ph2 : 0;
   h.n_reqs = n;
   h.total_tiles = (uint32_t)tiles;
   h.max_primes = max_primes;
@@ -354,7 +359,7 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
   {
     KTimer kt(c, kKInit, st);
     SV_TRY_CUDA(launch_init(ws.hdr.p, ws.slots.p, n, ws.bucket_count.p, mode == 0 ? ws.stage_cnt.p : nullptr,
-                            ws.total_tiles, ws.reqs.p, g.mw, c->d_p, c->n_primes, st));
+                            ws.total_tiles, ws.reqs.p, g.mw, c->d_p, c->n_primes, p_hyb_sq(g), st));
     kt.done();
   }
   c->launches++;
@@ -484,7 +489,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
     // sized for the buffers (the kernel reads the launch's sizes from the header)
     if (!e) e = launch_init(ws.hdr.p, ws.slots.p, (uint32_t)std::min<size_t>(ws.slots.cap, 1u << 20), ws.bucket_count.p,
                             mode == 0 ? ws.stage_cnt.p : nullptr, (uint32_t)std::min<size_t>(ws.bucket_count.cap, 1u << 30),
-                            ws.reqs.p, g.mw, c->d_p, c->n_primes, st);
+                            ws.reqs.p, g.mw, c->d_p, c->n_primes, p_hyb_sq(g), st);
     if (!e && pt.n > g.i_large) {
       BucketArgs b{};
       b.pt = pt;

@@ -227,9 +227,14 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_
   const int64_t ws = R.w0 - (int64_t)g.mw;
   const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws), E = R.jhi;
   if (E <= A) return;
-  const uint64_t ph = g.p_hyb, ph2 = ph * ph;
+  const uint64_t ph = g.p_hyb;
   const uint64_t mlo = 2 * A + 1, mhi = 2 * E - 1;
-  const uint64_t jmax = mhi / ph2;
+  const uint64_t jmax = R.j_max;  // floor(mhi / p_hyb^2), planned once per range
+  // a slice past the range's multipliers has nothing to do (a long range
+  // spreads its small multipliers' words over every slice, below)
+  if (E - A < (1ull << 30) && (uint64_t)s * (blockDim.x >> 5) >= kWarpJ &&
+      2 * (kWarpJ + (uint64_t)s * blockDim.x) + 1 > jmax)
+    return;  // uniform over the block
   const uint64_t p_top = a.pt.p[R.n_primes - 1];  // primes with p^2 < hi
   const uint64_t w_end = a.pt.bits_words;
   if (E - A >= (1ull << 30)) {
@@ -312,8 +317,11 @@ __global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_ke
   const uint32_t n_chunks = (n_reqs + kFillReqChunk - 1) / kFillReqChunk;
   const uint32_t px = min(fi.px, n_pblocks), py = min(fi.py, n_chunks);
   const uint32_t n_bar = px * py;  // <= 4096 * 64
-  // multiplier items actually present
-  const uint32_t jx = (max_primes > g.i_hyb && g.p_hyb != 0xFFFFFFFFu) ? fi.jx : 0u;
+  // multiplier items actually present: one thread per odd multiplier of the
+  // launch's largest range, at least eight slices, at most the captured ones
+  const uint64_t jm = a.hdr->j_max;
+  const uint32_t jx_need = (uint32_t)min((jm / 2 + kFillThreads) / kFillThreads, (uint64_t)fi.jx);
+  const uint32_t jx = (max_primes > g.i_hyb && g.p_hyb != 0xFFFFFFFFu) ? min(fi.jx, max(jx_need, 8u)) : 0u;
   const uint32_t jy = min(fi.jy, n_reqs);
   const uint32_t n_mult = jx * jy;  // <= 64 * 1024
   // Blocks take items round robin.  The multiplier items come first, slice

@@ -207,6 +207,8 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
     const uint64_t A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
     d.sq_lo = (uint32_t)host_isqrt(2 * A);
     d.sq_hi = d.jhi ? (uint32_t)host_isqrt(2 * d.jhi - 1) : 0u;
+    const uint64_t ph2 = g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb;
+    d.j_max = (ph2 && d.jhi) ? (2 * d.jhi - 1) / ph2 : 0;
   }
   d.list_cap = kNaList;
   d.fail_cap = kNaFail;
@@ -235,6 +237,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
     h.n_reqs = 1;
     h.total_tiles = d.n_tiles;
     h.max_primes = d.n_primes;
+    h.j_max = d.j_max;
     LaunchHeader *d_hdr = (LaunchHeader *)(base + L.hdr);
     ReqDesc *d_req = (ReqDesc *)(base + L.req);
     ResultSlot *d_slot = (ResultSlot *)(base + L.slot);
@@ -245,7 +248,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
       return SV_ECUDA;
     // the array keeps the previous call's contents: the counters, the result
     // slot and the bucket counts are cleared on the device first
-    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, d_req, g.mw, c->d_p, c->n_primes, st) != cudaSuccess)
+    if (launch_init(d_hdr, d_slot, 1, d_bcount, nullptr, d.n_tiles, d_req, g.mw, c->d_p, c->n_primes, 0, st) != cudaSuccess)
       return SV_ECUDA;
     c->launches++;
     if (d.n_primes > g.i_large) {

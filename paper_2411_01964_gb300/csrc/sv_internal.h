@@ -72,6 +72,9 @@ struct ReqDesc {
   // roots of the ends of its odd-multiple interval, set by the init kernel
   uint32_t sq_lo, sq_hi;
   uint32_t pad;
+  // the largest odd multiplier j with j p_hyb^2 <= 2 jhi - 1 (the bucket fill's
+  // multiplier items; 0: none), planned with n_primes
+  uint64_t j_max;
   uint32_t *bitmap_out; // sieve_only: word (a - w0) receives absolute word a
   // scan from device memory (the plain path): bitmap word (a - bitmap_w0)
   // holds absolute word a for every word of the range's windows; the tile
@@ -108,6 +111,7 @@ struct LaunchHeader {
   unsigned long long strag_count;
   uint32_t status;
   uint32_t pad2;
+  unsigned long long j_max;  // max over requests of ReqDesc::j_max (trims the bucket fill's multiplier slices)
 };
 
 struct Geometry {
@@ -193,7 +197,7 @@ struct CompactArgs {
 // Kernel launchers (defined in the .cu files).
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, ReqDesc *reqs, uint32_t mw,
-                        const uint32_t *primes, uint32_t n_table, cudaStream_t st);
+                        const uint32_t *primes, uint32_t n_table, uint64_t ph2, cudaStream_t st);
 cudaError_t launch_compact(const CompactArgs &a, uint32_t grid, cudaStream_t st);
 // n_large_max, n_reqs: upper bounds of the launch's bucket primes and ranges;
 // j_max: the largest odd multiplier any range needs for the primes >= p_hyb.

@@ -170,7 +170,7 @@ __device__ __forceinline__ void strike(uint32_t *win, uint32_t b) {
 // itself for launches of few ranges.
 // ---------------------------------------------------------------------------
 __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *bucket_count, uint32_t *stage_cnt,
-                            ReqDesc *reqs, uint32_t mw, const uint32_t *primes, uint32_t n_table) {
+                            ReqDesc *reqs, uint32_t mw, const uint32_t *primes, uint32_t n_table, uint64_t ph2) {
   const uint32_t n_slots = hdr->n_reqs, n_tiles = hdr->total_tiles;
   const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t gs = gridDim.x * blockDim.x;
@@ -190,6 +190,7 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
       else hi = mid;
     }
     R.n_primes = lo;
+    R.j_max = (ph2 && R.jhi) ? (2 * R.jhi - 1) / ph2 : 0;
   }
   for (uint32_t i = gid; i < n_tiles; i += gs) {
     bucket_count[i] = 0;
@@ -212,13 +213,13 @@ __global__ void init_kernel(LaunchHeader *hdr, ResultSlot *slots, uint32_t *buck
 
 cudaError_t launch_init(LaunchHeader *hdr, ResultSlot *slots, uint32_t n_slots,
                         uint32_t *bucket_count, uint32_t *stage_cnt, uint32_t n_tiles, ReqDesc *reqs, uint32_t mw,
-                        const uint32_t *primes, uint32_t n_table, cudaStream_t st) {
+                        const uint32_t *primes, uint32_t n_table, uint64_t ph2, cudaStream_t st) {
   uint64_t work = (uint64_t)n_slots * kMaxK;
   if (n_tiles > work) work = n_tiles;
   uint32_t grid = (uint32_t)((work + 255) / 256);
   if (grid < 1) grid = 1;
   if (grid > 1024) grid = 1024;
-  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt, reqs, mw, primes, n_table);
+  init_kernel<<<grid, 256, 0, st>>>(hdr, slots, bucket_count, stage_cnt, reqs, mw, primes, n_table, ph2);
   return cudaGetLastError();
 }
 
