@@ -415,6 +415,16 @@ sv_status sv_measure_peaks(sv_ctx *ctx, sv_peaks *out);
  */
 sv_status sv_inject_alloc_failures(sv_ctx *ctx, uint32_t count);
 
+/*
+ * Test hook for the bounded waits: the next `count` plain-path launches of
+ * this context (sv_verify_range_plain, sv_launch_range_plain) leave out their
+ * bulk window loads and wait at most about half a millisecond for them, so
+ * every block's bounded wait runs out; the call returns SV_ETIMEDOUT and the
+ * context stays usable.  Nothing is in flight when a block gives up: no GPU
+ * fault, trap or hang is involved.  count = 0 clears the hook.
+ */
+sv_status sv_inject_bulk_timeout(sv_ctx *ctx, uint32_t count);
+
 /* Number of kernels this context has launched so far. */
 uint64_t sv_kernel_launches(const sv_ctx *ctx);
 

@@ -95,6 +95,7 @@ _SIGS = {
     "sv_kernel_launches": (u64, [_CTX]),
     "sv_measure_peaks": (ctypes.c_int, [_CTX, P(sv_peaks)]),
     "sv_inject_alloc_failures": (ctypes.c_int, [_CTX, u32]),
+    "sv_inject_bulk_timeout": (ctypes.c_int, [_CTX, u32]),
     "sv_kernel_timing": (ctypes.c_int, [_CTX, ctypes.c_int]),
     "sv_kernel_time": (ctypes.c_int, [_CTX, ctypes.c_int, P(ctypes.c_double), P(u64)]),
 }
@@ -338,3 +339,8 @@ def sv_measure_peaks(ctx) -> dict:
 def sv_inject_alloc_failures(ctx, count: int) -> None:
     """Test hook: the next `count` buffer allocations of the library fail."""
     check(load().sv_inject_alloc_failures(ctx, count), "sv_inject_alloc_failures")
+
+
+def sv_inject_bulk_timeout(ctx, count: int) -> None:
+    """Test hook: the next `count` plain-path launches let their bounded bulk-load waits run out."""
+    check(load().sv_inject_bulk_timeout(ctx, count), "sv_inject_bulk_timeout")

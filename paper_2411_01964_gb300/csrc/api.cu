@@ -274,6 +274,11 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   if (hi_max > 1) max_primes = primes_upto(c, host_isqrt(hi_max - 1));
   LaunchHeader h{};
   h.j_max = (ph2 && jhi_max) ? (2 * jhi_max - 1) / ph2 : 0;
+  if (all_from_bitmap && ws.inject_bulk_timeouts) {  // the test hook of sv_inject_bulk_timeout
+    --ws.inject_bulk_timeouts;
+    h.skip_bulk_loads = 1;
+    h.bulk_wait_cycles = 1u << 20;  // about half a millisecond
+  }
   h.n_reqs = n;
   h.total_tiles = (uint32_t)tiles;
   h.max_primes = max_primes;
@@ -1420,6 +1425,13 @@ sv_status sv_last_transfer(const sv_ctx *c, uint64_t *h2d, uint64_t *d2h) {
 }
 
 uint64_t sv_kernel_launches(const sv_ctx *c) { return c ? c->launches.load() : 0; }
+
+sv_status sv_inject_bulk_timeout(sv_ctx *c, uint32_t count) {
+  if (!c) return SV_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->ws.inject_bulk_timeouts = count;
+  return SV_OK;
+}
 
 sv_status sv_inject_alloc_failures(sv_ctx *c, uint32_t count) {
   if (!c) return SV_EINVAL;

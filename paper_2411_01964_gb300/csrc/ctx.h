@@ -116,6 +116,7 @@ struct Workspace {
   bool all_from_bitmap = false;  // every range reads its windows from a bitmap: no bucket fill
   int tile_kernel_id = 2;        // per-kernel timing id of this workspace's tile kernel launches
   uint64_t j_max = 0;  // largest odd-multiplier count of the launch (bucket fill by j)
+  uint32_t inject_bulk_timeouts = 0;  // plain-path launches still to run with their bulk loads left out (test hook)
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
   // the captured launch graph and what it was captured for
   cudaGraphExec_t gexec = nullptr;

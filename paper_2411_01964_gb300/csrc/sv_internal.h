@@ -112,6 +112,13 @@ struct LaunchHeader {
   uint32_t status;
   uint32_t pad2;
   unsigned long long j_max;  // max over requests of ReqDesc::j_max (trims the bucket fill's multiplier slices)
+  // the scan pass's bounded wait for a window's bulk load, in SM clocks (0:
+  // the default, about a second); with skip_bulk_loads set the loads are not
+  // issued at all, so every wait runs out (sv_inject_bulk_timeout tests that
+  // path; nothing is in flight when the blocks give up)
+  unsigned long long bulk_wait_cycles;
+  uint32_t skip_bulk_loads;
+  uint32_t pad3;
 };
 
 struct Geometry {

@@ -744,8 +744,10 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       // words), and the bitmap is allocated with 4 words of room behind it
       const uint32_t cnt4 = (cnt + 3u) & ~3u;
       const bool bulk = cnt && (nz0 & 3u) == 0u && ((uintptr_t)src & 15u) == 0u && nz0 + cnt4 <= g.tw + g.mw;
+      const bool skip = a.hdr->skip_bulk_loads != 0u;  // the test hook: nothing is issued, the wait runs out
+      const long long wait_cycles = a.hdr->bulk_wait_cycles ? (long long)a.hdr->bulk_wait_cycles : kBulkWaitCycles;
       if (bulk) {
-        if (tid == 0) {
+        if (tid == 0 && !skip) {
           fence_proxy_async_smem();  // the previous tile's reads of the window come first
           const uint32_t bytes = 4u * cnt4;
           mbar_arrive_expect_tx(&sh.load_bar, bytes);
@@ -761,13 +763,13 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
         sh.need = need;
       }
       if (bulk) {
-        bool ok = mbar_wait_bounded(&sh.load_bar, load_parity, kBulkWaitCycles);
+        bool ok = mbar_wait_bounded(&sh.load_bar, load_parity, wait_cycles);
         if (__syncthreads_or(!ok)) {
           // the copy did not arrive in time: report it, wait once more for
           // the copy in flight (it writes into this block's shared memory),
           // and stop this block
           if (tid == 0) atomicOr(&a.hdr->status, kStTimeout);
-          ok = mbar_wait_bounded(&sh.load_bar, load_parity, kBulkWaitCycles);
+          ok = mbar_wait_bounded(&sh.load_bar, load_parity, wait_cycles);
           __syncthreads_or(!ok);
           return;
         }

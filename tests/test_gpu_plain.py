@@ -92,3 +92,19 @@ def test_sieve_bitmap_unaligned_buffer(gpu, orc):
     f0 = (first - 1) // 2 - 32 * (lo // 64)
     cnt = (hi - first + 1) // 2
     assert np.array_equal(bits[f0:f0 + cnt], orc.sieve_odd(lo, hi))
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable(orc):
+    # the scan pass's wait for a window's bulk load is bounded; with the loads
+    # left out on purpose (nothing in flight), every block gives up, the call
+    # returns SV_ETIMEDOUT, and the next calls are correct
+    from paper_2411_01964_gb300 import B
+    lo, hi = (1 << 40) + 12345, (1 << 40) + 12345 + (1 << 23) + 777
+    with Verifier(max_hi=1 << 41) as v:
+        B.sv_inject_bulk_timeout(v.ctx, 1)
+        with pytest.raises(B.SvError) as e:
+            v.verify_range_plain(lo, hi)
+        assert e.value.status == B.SV_ETIMEDOUT
+        o = orc.verify_range(lo, hi, per_n=True)
+        assert_same_range(v.verify_range_plain(lo, hi, per_n=True), o)
+        assert_same_range(v.verify_range(lo, hi, per_n=True), o)
