@@ -217,6 +217,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   uint64_t tiles = 0, list_total = 0, fail_total = 0;
   uint32_t max_primes = 0;
   uint64_t jhi_max = 0;  // the largest odd multiplier floor((2 jhi - 1) / p_hyb^2) grows with jhi
+  uint64_t span_max = 0;  // the longest range, in bits
   uint64_t hi_max = 0;   // and the largest prime count with hi
   const uint64_t ph2 = g.p_hyb == 0xFFFFFFFFu ? 0 : (uint64_t)g.p_hyb * g.p_hyb;
   bool any_per_n = false;
@@ -256,6 +257,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
       d.n_primes = kPlanOnDevice;
     }
     if (nt && d.jhi > jhi_max) jhi_max = d.jhi;
+    if (nt && d.jhi - d.jlo > span_max) span_max = d.jhi - d.jlo;
     d.per_n_k = s.d_per_n;
     any_per_n |= (s.d_per_n != nullptr);
     d.list_off = list_total;
@@ -274,6 +276,7 @@ sv_status plan(sv_ctx *c, const std::vector<RangeSpec> &specs, const Geometry &g
   if (hi_max > 1) max_primes = primes_upto(c, host_isqrt(hi_max - 1));
   LaunchHeader h{};
   h.j_max = (ph2 && jhi_max) ? (2 * jhi_max - 1) / ph2 : 0;
+  h.fill_span = span_max;
   if (all_from_bitmap && ws.inject_bulk_timeouts) {  // the test hook of sv_inject_bulk_timeout
     --ws.inject_bulk_timeouts;
     h.skip_bulk_loads = 1;
@@ -446,7 +449,7 @@ sv_status enqueue(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_t st) 
       ca.stage_cnt = ws.stage_cnt.p;
       ca.stage_cap = g.stage_cap;
       KTimer kt(c, kKCompact, st);
-      SV_TRY_CUDA(launch_compact(ca, std::min<uint32_t>((ws.total_tiles + 1023) / 1024, (uint32_t)c->num_sms), st));
+      SV_TRY_CUDA(launch_compact(ca, std::min<uint32_t>((ws.total_tiles + 127) / 128, 4u * (uint32_t)c->num_sms), st));
       kt.done();
       c->launches++;
     }
@@ -558,7 +561,7 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       ca.stage_k = ws.stage_k.p;
       ca.stage_cnt = ws.stage_cnt.p;
       ca.stage_cap = g.stage_cap;
-      e = launch_compact(ca, (uint32_t)c->num_sms, st);
+      e = launch_compact(ca, 4u * (uint32_t)c->num_sms, st);  // blocks of 128 tiles, grid-stride
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(st, &graph);

@@ -8,7 +8,9 @@
 // block-stride loop, so that the two run side by side:
 //   * Barrett items (prime block, request chunk): primes i_large <= i < i_hyb,
 //     one thread per prime; one Barrett reduction per range gives its first
-//     struck bit, then the thread walks the further hits;
+//     struck bit, then the thread walks the further hits (for a launch of
+//     few ranges, the blocks of the smallest primes, which have the most
+//     hits, are cut into segments of the range, one item each);
 //   * multiplier items (slice, request): primes p >= p_hyb, reached through
 //     their odd multipliers j (j p^2 in the range) and the prime bitmap.
 // A bucket slot is reserved with a global atomic that returns the slot; a
@@ -27,6 +29,16 @@ constexpr uint32_t kFillThreads = 256;
 constexpr uint32_t kFillReqChunk = 64;  // ranges per Barrett item
 constexpr uint32_t kHitBatch = 4;       // slot reservations in flight per thread
 constexpr uint64_t kWarpJ = 32;         // odd j < 2 kWarpJ are handled cooperatively (warp or grid)
+// A launch of one request chunk (a single range, a sweep chunk) cuts the
+// Barrett prime blocks whose smallest prime would walk more than kSegHits
+// hits into up to kMaxSeg segments of each range, one item each.  A thread's
+// hits are a chain of slot reservations, each a global atomic round trip
+// (about half a microsecond under load), so a segment holds two batches of
+// kHitBatch: the smallest primes' hits spread over many blocks instead.
+constexpr uint64_t kSegHits = 2 * kHitBatch;
+constexpr uint32_t kMaxSeg = 64;  // a power of two
+constexpr uint32_t kMaxSplitBlocks = 16;  // prime blocks that may be cut
+constexpr uint32_t kMaxSplitExtra = kMaxSplitBlocks * (kMaxSeg - 1);
 
 struct FillReq {
   uint64_t A, E;  // struck bits wanted: [A, E)
@@ -95,10 +107,21 @@ __device__ __forceinline__ void bucket_emit(const BucketArgs &a, const uint64_t 
 }
 
 // ---- Barrett items ----------------------------------------------------------
-// Primes of prime block pb (one per thread) against the ranges of request
-// chunk rc.
-__device__ void fill_barrett_item(const BucketArgs &a, FillReq *s_req, uint32_t pb, uint32_t rc, uint32_t n_reqs,
-                                  uint32_t prime_end) {
+// Segments of prime block pb: the power of two at or above (span / q) /
+// kSegHits for its smallest prime's q (the Barrett estimate of span / q is at
+// most 2 low), 1 to kMaxSeg.
+__device__ __forceinline__ uint32_t seg_count(const BucketArgs &a, uint32_t pb, uint64_t span) {
+  const uint32_t i = a.g.i_large + pb * kFillThreads;
+  const uint64_t hits = __umul64hi(span, a.pt.mu[i]);
+  uint32_t n = 1;
+  while (n < kMaxSeg && (uint64_t)n * kSegHits < hits) n <<= 1;
+  return n;
+}
+
+// Primes of prime block pb (one per thread) against segment seg of nseg of
+// each range of request chunk rc.
+__device__ void fill_barrett_item(const BucketArgs &a, FillReq *s_req, uint32_t pb, uint32_t seg, uint32_t nseg,
+                                  uint32_t rc, uint32_t n_reqs, uint32_t prime_end) {
   const uint32_t r0 = rc * kFillReqChunk;
   const uint32_t nr = min(kFillReqChunk, n_reqs - r0);
   __syncthreads();  // s_req holds the previous item's ranges
@@ -108,6 +131,12 @@ __device__ void fill_barrett_item(const BucketArgs &a, FillReq *s_req, uint32_t 
     const int64_t ws = R.w0 - (int64_t)a.g.mw;
     f.A = 32ull * (uint64_t)(ws < 0 ? 0 : ws);
     f.E = R.jhi;
+    if (nseg > 1 && f.E > f.A) {  // the segment's bits [A + seg L, A + (seg + 1) L), L = ceil((E - A) / nseg)
+      const uint64_t len = (f.E - f.A + nseg - 1) >> (31 - __clz(nseg));  // nseg: a power of two
+      const uint64_t a0 = f.A + seg * len;
+      f.A = a0 < f.E ? a0 : f.E;
+      if (f.E - f.A > len) f.E = f.A + len;
+    }
     f.w0 = R.w0;
     f.tile_base = R.tile_base;
     f.n_tiles = R.n_tiles;
@@ -259,16 +288,19 @@ __device__ void fill_mult_item(const BucketArgs &a, uint64_t (*s_iv)[3], uint32_
       if (t == kWarpJ - 1) s_iv[kWarpJ][2] = incl;
     }
     __syncthreads();
-    // the words of all small multipliers, one per thread of the item's slices
-    const uint64_t total = s_iv[kWarpJ][2];
-    for (uint64_t gw = (uint64_t)s * blockDim.x + threadIdx.x; gw < total; gw += (uint64_t)nsl * blockDim.x) {
+    // the words of all small multipliers, a quarter word (8 odd p) per
+    // thread of the item's slices: each prime is a chain of slot
+    // reservations, so the primes spread over as many threads as possible
+    const uint64_t total = 4 * s_iv[kWarpJ][2];
+    for (uint64_t gq = (uint64_t)s * blockDim.x + threadIdx.x; gq < total; gq += (uint64_t)nsl * blockDim.x) {
+      const uint64_t gw = gq >> 2;
       uint32_t t = 0;  // the last multiplier whose words start at or below gw
 #pragma unroll
       for (uint32_t h = kWarpJ / 2; h > 0; h >>= 1)
         if (t + h < kWarpJ && s_iv[t + h][2] <= gw) t += h;
       const uint64_t b0 = s_iv[t][0], b1 = s_iv[t][1];
       const uint64_t w = (b0 >> 5) + (gw - s_iv[t][2]);
-      emit_word(a, R, interval_word(a, w, b0, b1), w, 2 * t + 1);
+      emit_word(a, R, interval_word(a, w, b0, b1) & (0xFFu << (8u * (uint32_t)(gq & 3u))), w, 2 * t + 1);
     }
   } else {
     const uint32_t lane = threadIdx.x & 31u;
@@ -315,8 +347,28 @@ __global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_ke
   const uint32_t prime_end = min(max_primes, g.i_hyb);
   const uint32_t n_pblocks = prime_end > g.i_large ? (prime_end - g.i_large + blockDim.x - 1) / blockDim.x : 0u;
   const uint32_t n_chunks = (n_reqs + kFillReqChunk - 1) / kFillReqChunk;
-  const uint32_t px = min(fi.px, n_pblocks), py = min(fi.py, n_chunks);
-  const uint32_t n_bar = px * py;  // <= 4096 * 64
+  // the first n_split prime blocks are cut into segments (one request chunk
+  // only): s_split[1] items for them, then one per remaining block (kept in
+  // shared memory, not registers, across the item loop)
+  __shared__ uint32_t s_split[2];
+  if (threadIdx.x == 0) {
+    uint32_t n_split = 0, split_items = 0;
+    const uint64_t span = a.hdr->fill_span;
+    if (n_chunks == 1 && span) {
+      while (n_split < min(kMaxSplitBlocks, n_pblocks)) {
+        const uint32_t ns = seg_count(a, n_split, span);
+        if (ns <= 1) break;
+        split_items += ns;
+        ++n_split;
+      }
+    }
+    s_split[0] = n_split;
+    s_split[1] = split_items;
+  }
+  __syncthreads();
+  const uint32_t n_pbs = s_split[1] + (n_pblocks - s_split[0]);  // (prime block, segment) items per chunk
+  const uint32_t px = min(fi.px, n_pbs), py = min(fi.py, n_chunks);
+  const uint32_t n_bar = px * py;  // <= (4096 + kMaxSplitExtra) * 64
   // multiplier items actually present: one thread per odd multiplier of the
   // launch's largest range, at least eight slices, at most the captured ones
   const uint64_t jm = a.hdr->j_max;
@@ -333,9 +385,25 @@ __global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_ke
       for (uint32_t r = it % jy; r < n_reqs; r += jy) fill_mult_item(a, s_iv, it / jy, jx, r);
     } else {
       const uint32_t m = it - n_mult;
-      // item (pbx, rcy) covers prime blocks pbx + px i and chunks rcy + py k
+      // item (x, rcy) covers (prime block, segment) items x + px i and
+      // chunks rcy + py k
       for (uint32_t rc = m / px; rc < n_chunks; rc += py)
-        for (uint32_t pb = m % px; pb < n_pblocks; pb += px) fill_barrett_item(a, s_req, pb, rc, n_reqs, prime_end);
+        for (uint32_t x = m % px; x < n_pbs; x += px) {
+          uint32_t pb, seg = 0, nseg = 1;
+          if (x < s_split[1]) {
+            pb = 0;
+            seg = x;
+            for (;;) {
+              nseg = seg_count(a, pb, a.hdr->fill_span);
+              if (seg < nseg) break;
+              seg -= nseg;
+              ++pb;
+            }
+          } else {
+            pb = s_split[0] + (x - s_split[1]);
+          }
+          fill_barrett_item(a, s_req, pb, seg, nseg, rc, n_reqs, prime_end);
+        }
     }
   }
 }
@@ -344,7 +412,8 @@ cudaError_t launch_bucket_fill(const BucketArgs &a, uint32_t n_large_max, uint32
                                uint32_t max_blocks, cudaStream_t st) {
   if (n_large_max == 0 || n_reqs == 0) return cudaSuccess;
   FillItems fi;
-  fi.px = (uint32_t)std::min<uint64_t>((n_large_max + kFillThreads - 1) / kFillThreads, 4096);
+  // prime blocks, plus the segments of the cut ones
+  fi.px = (uint32_t)std::min<uint64_t>((n_large_max + kFillThreads - 1) / kFillThreads, 4096) + kMaxSplitExtra;
   fi.py = std::min<uint32_t>((n_reqs + kFillReqChunk - 1) / kFillReqChunk, 64);
   const bool mult = a.g.p_hyb != 0xFFFFFFFFu && j_max != 0;
   // slices: one thread per odd multiplier (at least eight slices, so that a

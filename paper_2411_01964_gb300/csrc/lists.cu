@@ -8,8 +8,9 @@
 namespace sv {
 
 // ---------------------------------------------------------------------------
-// The ordered list (mode 0).  The launch's tiles are cut into blocks of 1024,
-// one thread per tile; a tile's place in its range's list is the number of
+// The ordered list (mode 0).  The launch's tiles are cut into blocks of 128,
+// one thread per tile (small blocks, so that a launch's tiles spread over
+// the SMs); a tile's place in its range's list is the number of
 // entries its range staged in the tiles before it: the block's inclusive
 // scan (segmented at range starts) plus, for a range that began in an
 // earlier block, the sum of its staged counts there.  Each tile's few
@@ -18,7 +19,8 @@ namespace sv {
 // not stored: the smallest ones are kept.  The thread of a range's last tile
 // writes the range's total.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kCompactBlock = 1024;
+constexpr uint32_t kCompactBlock = 128;
+constexpr uint32_t kCompactWarps = kCompactBlock / 32;
 constexpr uint32_t kRankRegs = 8;  // staged entries of a tile ranked in registers (more: from memory)
 static_assert(kRankRegs % 2 == 0 && kRankRegs <= kStageCap, "the vector loads read whole pairs inside one slot");
 
@@ -31,9 +33,9 @@ __device__ __forceinline__ uint32_t range_of_tile(const ReqDesc *reqs, uint32_t 
   return lo;
 }
 
-__global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactArgs a) {
+__global__ void __launch_bounds__(kCompactBlock) list_compact_kernel(CompactArgs a) {
   __shared__ uint32_t incl_s[kCompactBlock];
-  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t wsum[kCompactWarps];
   __shared__ uint32_t carry_s;
   const uint32_t n_reqs = a.hdr->n_reqs, total = a.hdr->total_tiles;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
@@ -46,6 +48,18 @@ __global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactA
     const ReqDesc *R = act ? &a.reqs[r] : nullptr;
     const bool listed = act && !R->sieve_only && t - R->tile_base < R->n_tiles;
     const uint32_t cnt = listed ? min(a.stage_cnt[t], a.stage_cap) : 0u;
+    // the tile's first kRankRegs staged entries and their k, loaded before
+    // the scan so that the loads overlap it (a tile's staging slot is
+    // 16-byte aligned and holds kStageCap >= kRankRegs entries: the loads
+    // stay inside it; entries past cnt are ignored)
+    ulonglong2 pre[kRankRegs / 2];
+    uint64_t pre_k = 0;
+    if (listed) {
+      const ulonglong2 *sn2 = reinterpret_cast<const ulonglong2 *>(a.stage_n + (size_t)t * kStageCap);
+#pragma unroll
+      for (uint32_t h = 0; h < kRankRegs / 2; ++h) pre[h] = sn2[h];
+      pre_k = *reinterpret_cast<const uint64_t *>(a.stage_k + (size_t)t * kStageCap);
+    }
     // carry-in: the staged entries of the block's first range before the block
     if (tid == 0) carry_s = 0;
     __syncthreads();
@@ -53,9 +67,23 @@ __global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactA
       const uint32_t r0 = range_of_tile(a.reqs, n_reqs, b0);
       const uint32_t tb0 = a.reqs[r0].tile_base;
       uint32_t part = 0;
-      if (!a.reqs[r0].sieve_only)
-  #pragma unroll 8
-        for (uint32_t u = tb0 + tid; u < b0; u += kCompactBlock) part += min(a.stage_cnt[u], a.stage_cap);
+      if (!a.reqs[r0].sieve_only && tb0 < b0) {
+        // 16-byte loads over the whole groups of four counts (the count
+        // array's start is 16-byte aligned; else one count at a time)
+        const uint32_t v0 = (tb0 + 3u) >> 2, v1 = b0 >> 2;
+        const bool vec = ((uintptr_t)a.stage_cnt & 15u) == 0u && v0 < v1;
+        const uint32_t s_end = vec ? 4u * v0 : b0;
+        for (uint32_t u = tb0 + tid; u < s_end; u += kCompactBlock) part += min(a.stage_cnt[u], a.stage_cap);
+        if (vec) {
+          const uint4 *c4 = reinterpret_cast<const uint4 *>(a.stage_cnt);
+#pragma unroll 8
+          for (uint32_t v = v0 + tid; v < v1; v += kCompactBlock) {
+            const uint4 x = c4[v];
+            part += min(x.x, a.stage_cap) + min(x.y, a.stage_cap) + min(x.z, a.stage_cap) + min(x.w, a.stage_cap);
+          }
+          for (uint32_t u = 4u * v1 + tid; u < b0; u += kCompactBlock) part += min(a.stage_cnt[u], a.stage_cap);
+        }
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
       if (lane == 0 && part) atomicAdd(&carry_s, part);
@@ -70,14 +98,14 @@ __global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactA
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      const uint32_t w = wsum[lane];
+      const uint32_t w = lane < kCompactWarps ? wsum[lane] : 0u;
       uint32_t wi = w;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
         if (lane >= (uint32_t)o) wi += y;
       }
-      wsum[lane] = wi - w;
+      if (lane < kCompactWarps) wsum[lane] = wi - w;
     }
     __syncthreads();
     incl += wsum[warp];
@@ -92,18 +120,13 @@ __global__ void __launch_bounds__(kCompactBlock, 1) list_compact_kernel(CompactA
       const uint8_t *sk = a.stage_k + (size_t)t * kStageCap;
       if (cnt <= kRankRegs) {
         // the usual case: a few entries, ranked in registers
-        // (a tile's staging slot is 16-byte aligned and holds kStageCap >=
-        // kRankRegs entries: the vector loads stay inside it)
         uint64_t v[kRankRegs];
-        const ulonglong2 *sn2 = reinterpret_cast<const ulonglong2 *>(sn);
 #pragma unroll
         for (uint32_t h = 0; h < kRankRegs / 2; ++h) {
-          ulonglong2 x = make_ulonglong2(~0ull, ~0ull);
-          if (2 * h < cnt) x = sn2[h];
-          v[2 * h] = x.x;
-          v[2 * h + 1] = 2 * h + 1 < cnt ? x.y : ~0ull;
+          v[2 * h] = 2 * h < cnt ? pre[h].x : ~0ull;
+          v[2 * h + 1] = 2 * h + 1 < cnt ? pre[h].y : ~0ull;
         }
-        const uint64_t ks = *reinterpret_cast<const uint64_t *>(sk);  // k of entry e: byte e
+        const uint64_t ks = pre_k;  // k of entry e: byte e
 #pragma unroll
         for (uint32_t e = 0; e < kRankRegs; ++e) {
           if (e >= cnt) break;

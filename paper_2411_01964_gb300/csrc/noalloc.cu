@@ -238,6 +238,7 @@ extern "C" sv_status sv_verify_range_noalloc(sv_ctx *c, uint64_t lo, uint64_t hi
     h.total_tiles = d.n_tiles;
     h.max_primes = d.n_primes;
     h.j_max = d.j_max;
+    h.fill_span = d.jhi - d.jlo;
     LaunchHeader *d_hdr = (LaunchHeader *)(base + L.hdr);
     ReqDesc *d_req = (ReqDesc *)(base + L.req);
     ResultSlot *d_slot = (ResultSlot *)(base + L.slot);

@@ -119,6 +119,10 @@ struct LaunchHeader {
   unsigned long long bulk_wait_cycles;
   uint32_t skip_bulk_loads;
   uint32_t pad3;
+  // the longest range of the launch, in bits (jhi - jlo): the bucket fill
+  // cuts the hits of its smallest Barrett primes into segments of the range
+  // when the launch has few ranges (0: no cut)
+  unsigned long long fill_span;
 };
 
 struct Geometry {
