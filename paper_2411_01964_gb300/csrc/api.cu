@@ -22,6 +22,12 @@ std::atomic<uint32_t> g_inject_alloc_failures{0};
 void Workspace::release_all() {
   if (gexec) cudaGraphExecDestroy(gexec);
   gexec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  graph = nullptr;
+  for (cudaEvent_t &e : gev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   if (staged) cudaEventDestroy(staged);
   staged = nullptr;
   reqs.release();
@@ -487,9 +493,18 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
   key.strag_cap = ws.strag_cap;
   key.req_copy = req_copy;
   key.n_table = c->n_primes;
+  // per-kernel timing of the tile kernel: event-record nodes around it
+  const bool timed = ((c->kprof >> ws.tile_kernel_id) & 1u) && st == c->stream;
+  key.timed = timed ? 1u : 0u;
   if (!ws.gexec || std::memcmp(&key, &ws.gkey, sizeof(key)) != 0) {
     if (ws.gexec) cudaGraphExecDestroy(ws.gexec);
     ws.gexec = nullptr;
+    if (ws.graph) cudaGraphDestroy(ws.graph);
+    ws.graph = nullptr;
+    ws.gnode[0] = ws.gnode[1] = nullptr;
+    if (timed)
+      for (cudaEvent_t &ev : ws.gev)
+        if (!ev && cudaEventCreate(&ev) != cudaSuccess) return SV_ECUDA;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SV_ECUDA;
     const PrimeTab pt = prime_tab(c);
     cudaError_t e = cudaMemcpyAsync(ws.reqs.p, ws.h_reqs.p, sizeof(ReqDesc) * req_copy, cudaMemcpyHostToDevice, st);
@@ -527,7 +542,9 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
         t.stage_k = ws.stage_k.p;
         t.stage_cnt = ws.stage_cnt.p;
       }
-      e = launch_tiles(t, c->cfg.threads, (uint32_t)c->num_sms * c->cfg.ctas_per_sm, 4ull * (g.tw + g.mw), mode, st);
+      if (timed) e = cudaEventRecordWithFlags(ws.gev[0], st, cudaEventRecordExternal);
+      if (!e) e = launch_tiles(t, c->cfg.threads, (uint32_t)c->num_sms * c->cfg.ctas_per_sm, 4ull * (g.tw + g.mw), mode, st);
+      if (!e && timed) e = cudaEventRecordWithFlags(ws.gev[1], st, cudaEventRecordExternal);
     }
     if (!e) {
       StragArgs sa{};
@@ -569,13 +586,41 @@ sv_status enqueue_graph(sv_ctx *c, const Geometry &g, Workspace &ws, cudaStream_
       if (graph) cudaGraphDestroy(graph);
       return SV_ECUDA;
     }
+    if (timed) {  // the two event-record nodes, found by their events
+      size_t nn = 0;
+      std::vector<cudaGraphNode_t> nodes;
+      cudaError_t e4 = cudaGraphGetNodes(graph, nullptr, &nn);
+      if (!e4) {
+        nodes.resize(nn);
+        e4 = cudaGraphGetNodes(graph, nodes.data(), &nn);
+      }
+      for (size_t i = 0; !e4 && i < nn; ++i) {
+        cudaGraphNodeType ty;
+        if ((e4 = cudaGraphNodeGetType(nodes[i], &ty)) || ty != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        if ((e4 = cudaGraphEventRecordNodeGetEvent(nodes[i], &ev))) break;
+        for (int k = 0; k < 2; ++k)
+          if (ev == ws.gev[k]) ws.gnode[k] = nodes[i];
+      }
+      if (e4 || !ws.gnode[0] || !ws.gnode[1]) {
+        cudaGraphDestroy(graph);
+        return SV_ECUDA;
+      }
+    }
     const cudaError_t e3 = cudaGraphInstantiate(&ws.gexec, graph, 0);
-    cudaGraphDestroy(graph);
     if (e3 != cudaSuccess) {
+      cudaGraphDestroy(graph);
       ws.gexec = nullptr;
       return SV_ECUDA;
     }
+    ws.graph = graph;  // kept: the exec's event nodes are addressed through it
     ws.gkey = key;
+  }
+  if (timed) {  // fresh events for this replay's tile kernel
+    cudaEvent_t a = pool_event(c), b = pool_event(c);
+    SV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(ws.gexec, ws.gnode[0], a));
+    SV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(ws.gexec, ws.gnode[1], b));
+    c->kev.push_back({ws.tile_kernel_id, a, b});
   }
   SV_TRY_CUDA(cudaGraphLaunch(ws.gexec, st));
   // the graph reads the staging when it runs: the next plan waits for it
@@ -1324,7 +1369,10 @@ sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_
   Geometry g = make_geometry(c, max_span_bits(c, specs));
   if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
   if ((s = plan(c, specs, g, c->ws))) return s;
-  if ((s = enqueue(c, g, c->ws, c->stream))) return s;
+  // the captured graph (fewer launch gaps), unless a kernel other than the
+  // tile kernel is being timed: a graph brackets only the tile kernel
+  const bool graph = (c->kprof & ~(1u << c->ws.tile_kernel_id)) == 0;
+  if ((s = graph ? enqueue_graph(c, g, c->ws, c->stream) : enqueue(c, g, c->ws, c->stream))) return s;
   c->pending = true;
   c->pending_plain = false;
   c->pending_specs = specs;

@@ -347,23 +347,28 @@ __global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_ke
   const uint32_t prime_end = min(max_primes, g.i_hyb);
   const uint32_t n_pblocks = prime_end > g.i_large ? (prime_end - g.i_large + blockDim.x - 1) / blockDim.x : 0u;
   const uint32_t n_chunks = (n_reqs + kFillReqChunk - 1) / kFillReqChunk;
-  // the first n_split prime blocks are cut into segments (one request chunk
-  // only): s_split[1] items for them, then one per remaining block (kept in
-  // shared memory, not registers, across the item loop)
+  // the first n_split = s_split[0] prime blocks are cut into s_nseg[pb]
+  // segments (one request chunk only): s_split[1] items for them, then one
+  // per remaining block.  Warp 0 computes the counts side by side (they do
+  // not grow with pb, so the cut blocks are those with more than one).
+  static_assert(kMaxSplitBlocks <= 32, "one lane per block that may be cut");
   __shared__ uint32_t s_split[2];
-  if (threadIdx.x == 0) {
-    uint32_t n_split = 0, split_items = 0;
+  __shared__ uint32_t s_nseg[kMaxSplitBlocks];
+  if (threadIdx.x < 32) {
+    const uint32_t l = threadIdx.x;
     const uint64_t span = a.hdr->fill_span;
-    if (n_chunks == 1 && span) {
-      while (n_split < min(kMaxSplitBlocks, n_pblocks)) {
-        const uint32_t ns = seg_count(a, n_split, span);
-        if (ns <= 1) break;
-        split_items += ns;
-        ++n_split;
-      }
+    uint32_t ns = 1;
+    if (n_chunks == 1 && span && l < min(kMaxSplitBlocks, n_pblocks)) ns = seg_count(a, l, span);
+    const uint32_t one = __ballot_sync(0xFFFFFFFFu, ns <= 1);  // lanes >= kMaxSplitBlocks vote here too
+    const uint32_t n_split = one ? (uint32_t)(__ffs(one) - 1) : 32u;
+    uint32_t items = l < n_split ? ns : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) items += __shfl_xor_sync(0xFFFFFFFFu, items, o);
+    if (l < kMaxSplitBlocks) s_nseg[l] = ns;
+    if (l == 0) {
+      s_split[0] = n_split;
+      s_split[1] = items;
     }
-    s_split[0] = n_split;
-    s_split[1] = split_items;
   }
   __syncthreads();
   const uint32_t n_pbs = s_split[1] + (n_pblocks - s_split[0]);  // (prime block, segment) items per chunk
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(kFillThreads, kFillBlocksPerSm) bucket_fill_ke
             pb = 0;
             seg = x;
             for (;;) {
-              nseg = seg_count(a, pb, a.hdr->fill_span);
+              nseg = s_nseg[pb];
               if (seg < nseg) break;
               seg -= nseg;
               ++pb;

@@ -77,7 +77,8 @@ struct GraphKey {
   Geometry g;
   uint32_t threads, ctas, mode, strag_cap;
   uint64_t req_copy;
-  uint32_t n_table, pad;
+  uint32_t n_table;
+  uint32_t timed;  // 1: event-record nodes bracket the tile kernel
 };
 
 // Everything one launch needs on the device, reused across launches.
@@ -118,9 +119,14 @@ struct Workspace {
   uint64_t j_max = 0;  // largest odd-multiplier count of the launch (bucket fill by j)
   uint32_t inject_bulk_timeouts = 0;  // plain-path launches still to run with their bulk loads left out (test hook)
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
-  // the captured launch graph and what it was captured for
+  // the captured launch graph and what it was captured for; a timed graph
+  // keeps its event-record nodes around the tile kernel (gnode), whose
+  // events are swapped for fresh ones before each replay
+  cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   GraphKey gkey{};
+  cudaGraphNode_t gnode[2] = {nullptr, nullptr};
+  cudaEvent_t gev[2] = {nullptr, nullptr};  // the events recorded at capture
   cudaEvent_t staged = nullptr;  // recorded after the launch's reads of the pinned staging
   void release_all();
 };
