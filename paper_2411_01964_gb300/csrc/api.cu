@@ -141,8 +141,12 @@ uint64_t max_span_bits(const sv_ctx *c, const std::vector<RangeSpec> &specs) {
 
 // span_bits > 0: primes are bucketed only if they hit any window of the launch
 // at most ~64 times, so that the bucket fill stays balanced (one thread walks
-// one prime's hits); smaller primes are struck per tile instead.
-Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
+// one prime's hits); smaller primes are struck per tile instead.  A launch of
+// at most kFillReqChunk ranges has those hits cut into segments by the fill,
+// so it buckets every prime from kSegmentedLargeMin up (measured best on
+// single ranges of 2^34 and 2^36 integers: a sparse prime costs every tile
+// some work, a bucketed one only the tiles it strikes).
+Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0, size_t n_ranges = 0) {
   const sv_config &k = c->cfg;
   Geometry g{};
   g.tw = 1u << (k.tile_log2 - 5);
@@ -164,7 +168,11 @@ Geometry make_geometry(const sv_ctx *c, uint64_t span_bits = 0) {
   while (h < g.i_dense && (uint64_t)c->h_p[h] * c->h_p[h] <= head_q) ++h;
   g.n_head = h - g.i_med;
   uint64_t lp = k.large_prime_min;
-  if (span_bits) lp = std::max<uint64_t>(lp, host_isqrt(span_bits / 64) + 1);
+  if (span_bits) {
+    uint64_t lp_span = host_isqrt(span_bits / 64) + 1;
+    if (n_ranges && n_ranges <= kFillReqChunk) lp_span = std::min(lp_span, kSegmentedLargeMin);
+    lp = std::max<uint64_t>(lp, lp_span);
+  }
   uint32_t il = primes_upto(c, lp - 1);
   if (il < g.i_dense) il = g.i_dense;
   if (il > g.i_dense + (uint32_t)kMaxSparsePrimes) il = g.i_dense + (uint32_t)kMaxSparsePrimes;
@@ -821,7 +829,7 @@ uint64_t list_cap_estimate(uint64_t n_odd, uint32_t T, uint64_t cap) {
 }
 
 // Accessors for the no-allocation entry point (noalloc.cu); none allocates.
-Geometry geometry_for_span(const sv_ctx *c, uint64_t span_bits) { return make_geometry(c, span_bits); }
+Geometry geometry_for_span(const sv_ctx *c, uint64_t span_bits) { return make_geometry(c, span_bits, 1); }
 PrimeTab prime_table_of(const sv_ctx *c) { return prime_tab(c); }
 uint32_t primes_upto_of(const sv_ctx *c, uint64_t x) { return primes_upto(c, x); }
 sv_status tile_smem_ready(sv_ctx *c) { return ensure_tile_smem(c); }
@@ -833,7 +841,7 @@ sv_status run_ranges(sv_ctx *c, std::vector<RangeSpec> &specs, sv_range_result *
                      Workspace &ws, bool graph) {
   sv_status s = ensure_tile_smem(c);
   if (s) return s;
-  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  Geometry g = make_geometry(c, max_span_bits(c, specs), specs.size());
   if (ws.bucket_cap > g.bucket_cap) g.bucket_cap = ws.bucket_cap;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if ((s = plan(c, specs, g, ws))) return s;
@@ -905,7 +913,7 @@ sv_status plain_specs(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n, uin
 sv_status plain_enqueue(sv_ctx *c, std::vector<RangeSpec> &sieve, std::vector<RangeSpec> &scan, cudaStream_t st) {
   sv_status s = ensure_tile_smem(c);
   if (s) return s;
-  Geometry g = make_geometry(c, max_span_bits(c, sieve.empty() ? scan : sieve));
+  Geometry g = make_geometry(c, max_span_bits(c, sieve.empty() ? scan : sieve), (sieve.empty() ? scan : sieve).size());
   if (c->ws_sieve.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws_sieve.bucket_cap;
   if (!sieve.empty()) {
     c->ws_sieve.force_general = true;  // no lists in the sieve pass: no staging, no compaction
@@ -945,7 +953,7 @@ void plain_retry(sv_ctx *c, Collect what, bool sieve_retry, std::vector<RangeSpe
   if (sieve_retry) {
     if (what == kRetryBucket)
       c->ws_sieve.bucket_cap =
-          std::max<uint32_t>(c->ws_sieve.bucket_cap, make_geometry(c, max_span_bits(c, sieve)).bucket_auto) * 4;
+          std::max<uint32_t>(c->ws_sieve.bucket_cap, make_geometry(c, max_span_bits(c, sieve), sieve.size()).bucket_auto) * 4;
     return;
   }
   if (what == kRetryStrag) c->ws.strag_cap *= 4;
@@ -980,7 +988,7 @@ sv_status run_plain(sv_ctx *c, std::vector<RangeSpec> &sieve, std::vector<RangeS
 sv_status launch_ranges_async(sv_ctx *c, std::vector<RangeSpec> &specs, Workspace &ws, cudaStream_t st) {
   sv_status s = ensure_tile_smem(c);
   if (s) return s;
-  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  Geometry g = make_geometry(c, max_span_bits(c, specs), specs.size());
   if (ws.bucket_cap > g.bucket_cap) g.bucket_cap = ws.bucket_cap;
   if ((s = plan(c, specs, g, ws))) return s;
   return enqueue_graph(c, g, ws, st);
@@ -994,7 +1002,7 @@ sv_status collect_ranges(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_rang
   if (what == kDone) ws.force_general = false;
   if (what == kRetryGeneral) ws.force_general = true;
   if (what == kRetryBucket)
-    ws.bucket_cap = std::max<uint32_t>(ws.bucket_cap * 4, make_geometry(c, max_span_bits(c, specs)).bucket_auto);
+    ws.bucket_cap = std::max<uint32_t>(ws.bucket_cap * 4, make_geometry(c, max_span_bits(c, specs), specs.size()).bucket_auto);
   if (what == kRetryStrag) ws.strag_cap *= 4;
   return s;
 }
@@ -1280,7 +1288,7 @@ sv_status sv_launch_batch(sv_ctx *c, const uint64_t *lo, const uint64_t *hi, siz
                                           c->cfg.list_capacity);
     specs[i].fail_cap = 16;
   }
-  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  Geometry g = make_geometry(c, max_span_bits(c, specs), specs.size());
   if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
   if ((s = plan(c, specs, g, c->ws))) return s;
   if ((s = enqueue_graph(c, g, c->ws, c->stream))) return s;
@@ -1304,7 +1312,7 @@ sv_status sv_fetch_batch(sv_ctx *c, sv_range_result *out, size_t count) {
   if (s) return s;
   if (what != kDone) {
     std::vector<RangeSpec> specs = c->pending_specs;
-    if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
+    if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs), specs.size()).bucket_cap * 4;
     if (what == kRetryStrag) c->ws.strag_cap *= 4;
     if (what == kRetryGeneral) c->ws.force_general = true;
     s = run_ranges(c, specs, outs.data(), c->stream, c->ws, true);
@@ -1366,7 +1374,7 @@ sv_status sv_launch_range(sv_ctx *c, uint64_t lo, uint64_t hi, uint8_t *d_per_n_
   specs[0].d_per_n = d_per_n_k;
   specs[0].list_cap = c->cfg.list_capacity;
   specs[0].fail_cap = 1024;
-  Geometry g = make_geometry(c, max_span_bits(c, specs));
+  Geometry g = make_geometry(c, max_span_bits(c, specs), specs.size());
   if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
   if ((s = plan(c, specs, g, c->ws))) return s;
   // the captured graph (fewer launch gaps), unless a kernel other than the
@@ -1407,7 +1415,7 @@ sv_status sv_fetch_range(sv_ctx *c, sv_range_result *out) {
   if (what != kDone) {
     // an overflow: repeat the range with grown buffers, blocking
     std::vector<RangeSpec> specs = c->pending_specs;
-    if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs)).bucket_cap * 4;
+    if (what == kRetryBucket) c->ws.bucket_cap = make_geometry(c, max_span_bits(c, specs), specs.size()).bucket_cap * 4;
     if (what == kRetryStrag) c->ws.strag_cap *= 4;
     if (what == kRetryGeneral) c->ws.force_general = true;
     s = run_ranges(c, specs, outs, c->stream, c->ws, false);
@@ -1560,7 +1568,7 @@ sv_status time_launch(sv_ctx *c, const std::vector<RangeSpec> &specs0, double *b
   }
   double best = 1e300;
   for (int rep = 0; rep < 3 && !s; ++rep) {
-    Geometry g = make_geometry(c, max_span_bits(c, specs));
+    Geometry g = make_geometry(c, max_span_bits(c, specs), specs.size());
     if (c->ws.bucket_cap > g.bucket_cap) g.bucket_cap = c->ws.bucket_cap;
     if ((s = plan(c, specs, g, c->ws))) break;
     if (cudaEventRecord(a, c->stream) != cudaSuccess) s = SV_ECUDA;
@@ -1660,7 +1668,7 @@ sv_status tune(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_config *chosen
     }
     {  // bucket depth: the automatic estimate, or twice it
       c->cfg = best;
-      const uint32_t cap_auto = make_geometry(c, max_span_bits(c, specs)).bucket_auto;
+      const uint32_t cap_auto = make_geometry(c, max_span_bits(c, specs), specs.size()).bucket_auto;
       for (uint32_t v : {0u, 2u * cap_auto}) {
         if (s) break;
         sv_config k = best;

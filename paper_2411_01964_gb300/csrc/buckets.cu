@@ -26,7 +26,6 @@
 namespace sv {
 
 constexpr uint32_t kFillThreads = 256;
-constexpr uint32_t kFillReqChunk = 64;  // ranges per Barrett item
 constexpr uint32_t kHitBatch = 4;       // slot reservations in flight per thread
 constexpr uint64_t kWarpJ = 32;         // odd j < 2 kWarpJ are handled cooperatively (warp or grid)
 // A launch of one request chunk (a single range, a sweep chunk) cuts the

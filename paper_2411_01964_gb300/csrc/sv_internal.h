@@ -232,6 +232,11 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
 constexpr int kMaxDensePrimes = 128;  // must match the tile kernel's shared arrays (four warps)
 constexpr int kDenseMinHits = 4;      // primes with at least this many strikes per window are "dense"
 constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)
+// Ranges per Barrett item of the bucket fill; a launch of at most this many
+// ranges (one request chunk) has its smallest bucketed primes' hits cut into
+// segments of the range, so it can bucket primes down to kSegmentedLargeMin.
+constexpr uint32_t kFillReqChunk = 64;
+constexpr uint64_t kSegmentedLargeMin = 4096;
 constexpr uint32_t kFillBlocksPerSm = 4;  // resident bucket-fill blocks per SM (the launch bounds)
 // Bucket primes below 2^mult_prime_log2 (sv_config) get one Barrett reduction
 // per range; larger ones are found through their odd multipliers j (j p^2 in
