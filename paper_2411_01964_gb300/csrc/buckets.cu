@@ -106,6 +106,21 @@ __device__ __forceinline__ void bucket_emit(const BucketArgs &a, const uint64_t 
 }
 
 // ---- Barrett items ----------------------------------------------------------
+// The hits J, J + q, ... below f.E of one Barrett prime in one range (or
+// segment), kHitBatch slot reservations at a time.
+__device__ __noinline__ void barrett_walk(const BucketArgs &a, const FillReq &f, uint64_t J, uint64_t q) {
+  for (; J < f.E; J += kHitBatch * q) {
+    uint64_t Jv[kHitBatch];
+    uint32_t n = 0;
+#pragma unroll
+    for (uint32_t u = 0; u < kHitBatch; ++u) {
+      Jv[u] = J + u * q;
+      if (Jv[u] < f.E) n = u + 1;
+    }
+    bucket_emit(a, Jv, n, f.w0, f.tile_base, f.n_tiles);
+  }
+}
+
 // Segments of prime block pb: the power of two at or above (span / q) /
 // kSegHits for its smallest prime's q (the Barrett estimate of span / q is at
 // most 2 low), 1 to kMaxSeg.
@@ -148,19 +163,22 @@ __device__ void fill_barrett_item(const BucketArgs &a, FillReq *s_req, uint32_t 
   if (pi >= prime_end) return;
   const uint64_t p = a.pt.p[pi];
   const uint64_t q = p * p, mu = a.pt.mu[pi];
-  for (uint32_t r = 0; r < nr; ++r) {
-    const FillReq f = s_req[r];
-    if (pi >= f.n_primes || f.n_tiles == 0 || f.E <= f.A) continue;
-    for (uint64_t J = f.A + first_strike(f.A, q, mu); J < f.E; J += kHitBatch * q) {
-      uint64_t Jv[kHitBatch];
-      uint32_t n = 0;
-#pragma unroll
-      for (uint32_t u = 0; u < kHitBatch; ++u) {
-        Jv[u] = J + u * q;
-        if (Jv[u] < f.E) n = u + 1;
-      }
-      bucket_emit(a, Jv, n, f.w0, f.tile_base, f.n_tiles);
-    }
+  // two ranges per step: their first-strike reductions are independent
+  // chains of 64-bit multiplies, so they overlap; a hit (rare for most
+  // primes and ranges) is then walked range by range
+  // (only the bounds are held across the pair; a walk reads the rest of its
+  // range from shared memory)
+  uint32_t r = 0;
+  for (; r + 1 < nr; r += 2) {
+    const uint64_t A0 = s_req[r].A, A1 = s_req[r + 1].A;
+    const uint64_t J0 = A0 + first_strike(A0, q, mu), J1 = A1 + first_strike(A1, q, mu);
+    if (J0 < s_req[r].E && pi < s_req[r].n_primes && s_req[r].n_tiles) barrett_walk(a, s_req[r], J0, q);
+    if (J1 < s_req[r + 1].E && pi < s_req[r + 1].n_primes && s_req[r + 1].n_tiles)
+      barrett_walk(a, s_req[r + 1], J1, q);
+  }
+  if (r < nr) {
+    const uint64_t J = s_req[r].A + first_strike(s_req[r].A, q, mu);
+    if (J < s_req[r].E && pi < s_req[r].n_primes && s_req[r].n_tiles) barrett_walk(a, s_req[r], J, q);
   }
 }
 
