@@ -77,7 +77,9 @@ __device__ __forceinline__ uint32_t stamp_step(uint32_t j, uint32_t d, uint32_t 
 // entry e of a table is the pattern of the words a = e (mod P).  Table A
 // holds {3, 11} (P = 1089) and table B {5, 7} (P = 1225), or A alone {3, 5}
 // (P = 225) when only two primes are stamped.  Consecutive words read
-// consecutive entries, so a warp's reads hit distinct banks.
+// consecutive entries, so a warp's reads hit distinct banks.  Each table is
+// extended by kExt entries past its period, so that a warp reads entries
+// e .. e + 63 (e < P) without a wrap.
 template <int NS>
 struct StampTab {
   static constexpr bool kTwo = NS >= 4;                   // two tables
@@ -85,7 +87,9 @@ struct StampTab {
   static constexpr uint32_t kQb0 = 25, kQb1 = 49;
   static constexpr uint32_t kPa = kQa0 * kQa1;
   static constexpr uint32_t kPb = kTwo ? kQb0 * kQb1 : 0u;
-  static constexpr uint32_t kSize = kPa + kPb;
+  static constexpr uint32_t kExt = 64;
+  static constexpr uint32_t kOffB = kPa + kExt;           // table B's first entry
+  static constexpr uint32_t kSize = kTwo ? kOffB + kPb + kExt : kPa + kExt;
   static constexpr int kCovered = kTwo ? 4 : 2;           // stamp_p(0 .. kCovered-1)
 };
 
@@ -101,22 +105,51 @@ __device__ __forceinline__ void build_stamp_tables(uint32_t *tab) {
   using T = StampTab<NS>;
   for (uint32_t e = threadIdx.x; e < T::kSize; e += blockDim.x) {
     uint32_t v;
-    if (e < T::kPa) v = stamp_pattern(32u * e, T::kQa0) | stamp_pattern(32u * e, T::kQa1);
-    else v = stamp_pattern(32u * (e - T::kPa), T::kQb0) | stamp_pattern(32u * (e - T::kPa), T::kQb1);
+    // (entries past the period repeat its start: the pattern has period P words)
+    if (e < T::kOffB) v = stamp_pattern(32u * e, T::kQa0) | stamp_pattern(32u * e, T::kQa1);
+    else v = stamp_pattern(32u * (e - T::kOffB), T::kQb0) | stamp_pattern(32u * (e - T::kOffB), T::kQb1);
     tab[e] = v;
   }
 }
 
-// Window words [nz, nwords) <- AND of the NS stamped patterns; thread tid
-// takes words tid, tid + S, ...  The table positions advance by S mod P; the
-// primes beyond the tables keep j[s], the offset of their first struck bit in
-// the current word (>= 32: none), which moving S words lowers by 32*S mod q.
+// Window words [nz, nwords) <- AND of the NS stamped patterns.  With the
+// tables alone (NS <= 4), warp w stamps 64-word steps w, w + nwarps, ...:
+// lane l takes words l and l + 32 of the step, whose table entries are e + l
+// and e + 32 + l for one position e per warp and table, advanced by
+// 64 nwarps mod P per step.  The last (nwords - nz) mod 64 words, and every
+// word when primes beyond the tables are stamped, go thread by thread: thread
+// tid takes words tid, tid + S, ...; the table positions advance by S mod P,
+// and the primes beyond the tables keep j[s], the offset of their first
+// struck bit in the current word (>= 32: none), which moving S words lowers
+// by 32*S mod q.
 template <int NS>
 __device__ __forceinline__ void stamp_window(uint32_t *win, const uint32_t *tab, uint32_t nz, uint32_t nwords,
                                              int64_t wstart) {
   using T = StampTab<NS>;
   constexpr int NX = NS - T::kCovered;
   const uint32_t S = blockDim.x;
+  if (NX == 0) {
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = S >> 5;
+    const uint32_t steps = (nwords - nz) >> 6;
+    if (warp < steps) {
+      const uint64_t aw = (uint64_t)(wstart + (int64_t)(nz + 64u * warp));  // >= 0
+      uint32_t ea = (uint32_t)(aw % T::kPa), eb = T::kTwo ? (uint32_t)(aw % (T::kTwo ? T::kPb : 1u)) : 0u;
+      const uint32_t da = (64u * nwarps) % T::kPa, db = T::kTwo ? (64u * nwarps) % (T::kTwo ? T::kPb : 1u) : 0u;
+      for (uint32_t st = warp; st < steps; st += nwarps) {
+        const uint32_t i = nz + 64u * st + lane;
+        uint32_t m0 = tab[ea + lane], m1 = tab[ea + 32u + lane];
+        if (T::kTwo) {
+          m0 |= tab[T::kOffB + eb + lane];
+          m1 |= tab[T::kOffB + eb + 32u + lane];
+        }
+        win[i] = ~m0;
+        win[i + 32u] = ~m1;
+        ea = min(ea + da, ea + da - T::kPa);  // unsigned: subtracts P once the sum reaches it
+        if (T::kTwo) eb = min(eb + db, eb + db - T::kPb);
+      }
+    }
+    nz += 64u * steps;  // the rest thread by thread, below
+  }
   uint32_t i = nz + threadIdx.x;
   if (i >= nwords) return;
   const uint64_t aw = (uint64_t)(wstart + (int64_t)i);  // >= 0 since i >= nz
@@ -131,7 +164,7 @@ __device__ __forceinline__ void stamp_window(uint32_t *win, const uint32_t *tab,
   }
   for (; i < nwords; i += S) {
     uint32_t m = tab[ea];
-    if (T::kTwo) m |= tab[T::kPa + eb];
+    if (T::kTwo) m |= tab[T::kOffB + eb];
 #pragma unroll
     for (int s = 0; s < NX; ++s) {
       const uint32_t q = stamp_p(T::kCovered + s) * stamp_p(T::kCovered + s);
@@ -485,8 +518,10 @@ __device__ __forceinline__ void scan_tile_lean(const uint32_t *win, const TileAr
     const uint32_t r5 = __popc(u0) + __popc(u1);                                    \
     c5t += r4 - r5;                                                                 \
     x5 += r5;                                                                       \
-    SV_DEFER(I0, u0)                                                                \
-    SV_DEFER(I1, u1)                                                                \
+    if (__any_sync(0xFFFFFFFFu, u0 | u1)) { /* rare: a word of the warp left after k = 5 */ \
+      SV_DEFER(I0, u0)                                                              \
+      SV_DEFER(I1, u1)                                                              \
+    }                                                                               \
   }
   if (need == 0u && ifl <= mw && nfull >= nwords - ifl && (nwords - mw) % (64u * nwarps) == 0u) {
     // every core word is in range and fully valid, and no first occurrence
