@@ -868,7 +868,12 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       for (uint32_t d = 0; d < nh; ++d) {
         const uint32_t q = sh.dense_q[d];
         const uint32_t step = S * q;  // <= the window's bits
-        for (uint32_t b = sh.dense_off[d] + tid * q; b < nbits; b += step) strike(win, b);
+        uint32_t b = sh.dense_off[d] + tid * q;
+        for (; b + step < nbits; b += 2u * step) {  // two strikes per trip (b + step < nbits <= 2^32 - 2^31)
+          strike(win, b);
+          strike(win, b + step);
+        }
+        if (b < nbits) strike(win, b);
       }
       // the other dense primes, one warp each in a snake order over the warps
       // (their strike counts fall with p); lane l strikes off + q (l + 32 m)
@@ -878,7 +883,12 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
           const uint32_t d = nh + rd * nw + ((rd & 1u) ? nw - 1u - warp : warp);
           if (d >= nd) break;
           const uint32_t q = sh.dense_q[d], step = 32u * q;  // step <= the window's bits
-          for (uint32_t b = sh.dense_off[d] + lane * q; b < nbits; b += step) strike(win, b);
+          uint32_t b = sh.dense_off[d] + lane * q;
+          for (; b + step < nbits; b += 2u * step) {
+            strike(win, b);
+            strike(win, b + step);
+          }
+          if (b < nbits) strike(win, b);
         }
       }
       // a full window's strikes carry to the next window: its first struck
