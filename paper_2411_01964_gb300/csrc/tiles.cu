@@ -135,6 +135,7 @@ __device__ __forceinline__ void stamp_window(uint32_t *win, const uint32_t *tab,
       const uint64_t aw = (uint64_t)(wstart + (int64_t)(nz + 64u * warp));  // >= 0
       uint32_t ea = (uint32_t)(aw % T::kPa), eb = T::kTwo ? (uint32_t)(aw % (T::kTwo ? T::kPb : 1u)) : 0u;
       const uint32_t da = (64u * nwarps) % T::kPa, db = T::kTwo ? (64u * nwarps) % (T::kTwo ? T::kPb : 1u) : 0u;
+#pragma unroll 2
       for (uint32_t st = warp; st < steps; st += nwarps) {
         const uint32_t i = nz + 64u * st + lane;
         uint32_t m0 = tab[ea + lane], m1 = tab[ea + 32u + lane];
