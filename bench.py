@@ -284,7 +284,11 @@ def bench_range(name: str, stream, flush, steps: int, pk: dict, knobs: dict) -> 
         B.sv_kernel_timing(v.ctx, False)
         v.fetch_range(list_cap=16)
         from paper_2411_01964_gb300 import _ResultBuffers
-        out = _ResultBuffers(1 << max(16, (int(6.85e-6 * n_odd * 1.1)).bit_length()), 1024, None)  # made once
+        out = _ResultBuffers(1 << max(16, (int(6.85e-6 * n_odd * 1.1)).bit_length()), 1024, None,
+                             pinned=True)  # made once, page-locked
+        for _ in range(2):  # untimed warm-up: the call's launch graph is captured here
+            B.check(B.sv_verify_range(v.ctx, lo, hi, out.res), "sv_verify_range")
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         e2e_steps = 3
         h2d = d2h = 0
@@ -306,7 +310,7 @@ def bench_range(name: str, stream, flush, steps: int, pk: dict, knobs: dict) -> 
                          "kernel_avg_ms": tile_s * 1e3, "smem_atomic_frac": strikes / tile_s / pk["smem_atomic_strike_per_s"],
                          "peak_source": "measured in this run (sv_measure_peaks)"},
             "e2e": {"value": n_odd * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d // e2e_steps,
-                    "d2h_bytes_per_step": d2h // e2e_steps},
+                    "d2h_bytes_per_step": d2h // e2e_steps, "host_buffers": "caller-owned, page-locked"},
             "result": {"hist": r.hist[1:16], "kmax": r.kmax, "failures": r.fail_len, "list_len": r.list_len}}
 
 
@@ -641,13 +645,15 @@ def main() -> int:
     # end to end: the blocking public call with host buffers
     e2e_steps = 0 if args.no_e2e else max(3, min(args.steps, 10))
     rr = res
+    from paper_2411_01964_gb300 import _ResultBuffers
+    # caller-owned host buffers, made once and page-locked before the timed region, as a C caller would; the list
+    # room is the power of two above the expected count (Table 2: a fraction 6.85e-6 of odd n has mink >= 6)
+    out = _ResultBuffers(1 << max(16, (int(6.85e-6 * n_odd * 1.1)).bit_length()), 1024, None, pinned=True)
+    for _ in range(2 if e2e_steps else 0):  # untimed warm-up: the call's launch graph is captured here
+        B.check(B.sv_verify_range(v.ctx, lo, hi, out.res), "sv_verify_range")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = d2h = 0
-    from paper_2411_01964_gb300 import _ResultBuffers
-    # caller-owned host buffers, made once, as a C caller would; the list room is the power of two above the
-    # expected count (Table 2: a fraction 6.85e-6 of odd n has mink >= 6)
-    out = _ResultBuffers(1 << max(16, (int(6.85e-6 * n_odd * 1.1)).bit_length()), 1024, None)
     for _ in range(e2e_steps):
         B.check(B.sv_verify_range(v.ctx, lo, hi, out.res), "sv_verify_range")
         a, b = v.last_transfer()
@@ -699,7 +705,7 @@ def main() -> int:
                                                 "dense-strike pattern on every SM"},
         "peaks": {**pk, "hbm_gbs": drv.get("hbm_gbs"), "hbm_source": "MEASURED_PEAKS.json (copy bandwidth)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // max(e2e_steps, 1),
-                "d2h_bytes_per_step": d2h // max(e2e_steps, 1)},
+                "d2h_bytes_per_step": d2h // max(e2e_steps, 1), "host_buffers": "caller-owned, page-locked"},
         "gpu_launches": launches,
         "kernels": {"tile_ms_per_step": tile_ms / max(tile_n, 1),
                     "bucket_fill_ms_per_step": bucket_ms / max(bucket_n, 1) if bucket_n else 0.0,

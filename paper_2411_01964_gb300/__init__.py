@@ -52,10 +52,19 @@ class _ResultBuffers:
     """Host buffers wired into an sv_range_result (fresh per call: the result
     keeps views of them)."""
 
-    def __init__(self, list_cap: int, fail_cap: int, n_per_n: int | None):
+    def __init__(self, list_cap: int, fail_cap: int, n_per_n: int | None, pinned: bool = False):
         self.res = B.sv_range_result()
-        self.list_n = np.zeros(max(list_cap, 1), dtype=np.uint64)
-        self.list_k = np.zeros(max(list_cap, 1), dtype=np.uint8)
+        if pinned:
+            # page-locked host memory: the library copies a single range's list
+            # straight into it (no staging, no host copy)
+            import torch
+            self._pinned = (torch.zeros(max(list_cap, 1), dtype=torch.int64, pin_memory=True),
+                            torch.zeros(max(list_cap, 1), dtype=torch.uint8, pin_memory=True))
+            self.list_n = self._pinned[0].numpy().view(np.uint64)
+            self.list_k = self._pinned[1].numpy()
+        else:
+            self.list_n = np.zeros(max(list_cap, 1), dtype=np.uint64)
+            self.list_k = np.zeros(max(list_cap, 1), dtype=np.uint8)
         self.fails = np.zeros(max(fail_cap, 1), dtype=np.uint64)
         self.per_n = np.zeros(max(n_per_n, 1), dtype=np.uint8) if n_per_n is not None else None
         r = self.res

@@ -677,6 +677,18 @@ uint64_t list_want(const RangeSpec &sp, const sv_range_result *o) {
 constexpr uint64_t kListRetryMax = 1ull << 26;  // larger lists are returned truncated, unordered
 
 // Waits for the launch, checks the device status word and copies results out.
+// Host memory the device can copy into directly (allocated or registered as
+// page-locked); null counts as pinned (nothing to copy).
+bool is_pinned(const void *p) {
+  if (!p) return true;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered pointer is not an error to keep
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_result **outs, Workspace &ws,
                   cudaStream_t st, Collect *what) {
   const uint32_t n = ws.n_reqs;
@@ -692,13 +704,26 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
         spec_end = std::max<uint64_t>(spec_end, ws.h_reqs.p[r].list_off + ws.h_reqs.p[r].list_cap);
     if (spec_end > kSpeculativeList) spec_end = 0;
   }
-  if (spec_end) {
+  // one range whose caller buffers are pinned host memory: its list region
+  // goes straight into them (no staging copy, no host copy afterwards); the
+  // entries past the list's length are left unspecified
+  bool direct = false;
+  uint64_t direct_m = 0;
+  if (spec_end && n == 1 && outs[0] && is_pinned(outs[0]->list) && is_pinned(outs[0]->list_k)) {
+    direct = true;
+    direct_m = std::min<uint64_t>(ws.h_reqs.p[0].list_cap, outs[0]->list_cap);
+    const uint64_t off = ws.h_reqs.p[0].list_off;
+    if (direct_m && outs[0]->list)
+      SV_TRY_CUDA(cudaMemcpyAsync(outs[0]->list, ws.list_n.p + off, 8 * direct_m, cudaMemcpyDeviceToHost, st));
+    if (direct_m && outs[0]->list_k)
+      SV_TRY_CUDA(cudaMemcpyAsync(outs[0]->list_k, ws.list_k.p + off, direct_m, cudaMemcpyDeviceToHost, st));
+  } else if (spec_end) {
     if (ws.h_list_n.ensure(spec_end) || ws.h_list_k.ensure(spec_end)) return SV_ENOMEM;
     SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_n.p, ws.list_n.p, 8 * spec_end, cudaMemcpyDeviceToHost, st));
     SV_TRY_CUDA(cudaMemcpyAsync(ws.h_list_k.p, ws.list_k.p, spec_end, cudaMemcpyDeviceToHost, st));
   }
   SV_TRY_CUDA(cudaStreamSynchronize(st));
-  uint64_t d2h = sizeof(LaunchHeader) + sizeof(ResultSlot) * n + 9 * spec_end;
+  uint64_t d2h = sizeof(LaunchHeader) + sizeof(ResultSlot) * n + (direct ? 9 * direct_m : 9 * spec_end);
   const uint32_t status = ws.h_hdr.p->status;
   if (status & kStBadTile) return SV_ECUDA;
   if (status & kStTimeout) return SV_ETIMEDOUT;
@@ -775,7 +800,7 @@ sv_status collect(sv_ctx *c, const std::vector<RangeSpec> &specs, sv_range_resul
     o->list_overflow = s.list_count > o->list_cap ? 1 : 0;
     const ReqDesc &d = ws.h_reqs.p[r];
     const uint64_t nl = std::min<uint64_t>(s.list_count, d.list_cap);
-    if (nl && (o->list || o->list_k)) {
+    if (nl && (o->list || o->list_k) && !direct) {
       const uint64_t m = std::min<uint64_t>(nl, o->list_cap);
       if (ws.ordered) {  // ascending already (list_compact_kernel)
         if (o->list) std::memcpy(o->list, ws.h_list_n.p + d.list_off, 8 * m);

@@ -251,6 +251,28 @@ def test_kernel_timing_selects_kernels():
         B.sv_kernel_timing(v.ctx, False)
 
 
+def test_pinned_list_buffers_take_the_direct_copy():
+    """A single range's list is copied straight into page-locked caller
+    buffers: the same histogram and the same ascending list (n, mink) as
+    through pageable buffers, also when the caller has room for only a prefix
+    (the smallest entries), and nothing is written past the caller's room."""
+    from paper_2411_01964_gb300 import _ResultBuffers, binding as B
+    lo, hi = (1 << 40) + 1, (1 << 40) + (1 << 30)
+    with Verifier(max_hi=hi + 1) as v:
+        for cap in (1 << 13, 16):
+            ref = _ResultBuffers(cap, 64, None)
+            B.check(B.sv_verify_range(v.ctx, lo, hi, ref.res), "pageable")
+            pin = _ResultBuffers(cap + 8, 64, None, pinned=True)
+            pin.list_n[:] = 7
+            pin.res.list_cap = cap  # the last 8 entries lie past the caller's room
+            B.check(B.sv_verify_range(v.ctx, lo, hi, pin.res), "pinned")
+            a, b = ref.result(), pin.result()
+            assert a.hist == b.hist and a.list_len == b.list_len and a.list_len > 16
+            assert np.array_equal(a.list_n, b.list_n) and np.array_equal(a.list_k, b.list_k)
+            assert len(b.list_n) == min(cap, b.list_len)
+            assert (pin.list_n[cap:] == 7).all()
+
+
 def test_batch_graph_replay_and_recapture(orc):
     """Consecutive batches replay one captured graph; a batch that needs larger
     buffers re-captures it.  Every result equals the oracle's."""
