@@ -102,6 +102,11 @@ typedef struct sv_config {
  * Result of one range, filled by sv_verify_range / sv_verify_batch / sv_poll.
  * The caller sets the buffer pointers and capacities (any may be NULL with
  * capacity 0) before the call; everything else is written by the library.
+ * Entries of list / list_k past min(list_len, list_cap) are unspecified (the
+ * library may write there, never past list_cap).  For a call of one range
+ * whose list / list_k are page-locked host memory (cudaHostAlloc or
+ * cudaHostRegister), the list is copied from the device straight into them;
+ * other buffers receive it through the library's own staging.
  */
 typedef struct sv_range_result {
     uint64_t lo, hi;          /* echoed */
