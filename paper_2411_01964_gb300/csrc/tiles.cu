@@ -870,7 +870,9 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
         const uint32_t q = sh.dense_q[d];
         const uint32_t step = S * q;  // <= the window's bits
         uint32_t b = sh.dense_off[d] + tid * q;
-        for (; b + step < nbits; b += 2u * step) {  // two strikes per trip (b + step < nbits <= 2^32 - 2^31)
+        // two strikes per trip, their atomics in flight together (b and step are both below the window's
+        // bits, so b + step cannot wrap)
+        for (; b + step < nbits; b += 2u * step) {
           strike(win, b);
           strike(win, b + step);
         }
