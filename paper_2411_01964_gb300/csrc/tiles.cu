@@ -639,19 +639,23 @@ __device__ __forceinline__ void scan_tile(const uint32_t *win, const TileArgs &a
 
 // The tile queue hands out chunks of consecutive tiles, so that one CTA works
 // a range's tiles in order and the primes' offsets carry from one window to
-// the next; the last 4 tiles per CTA go one at a time, which keeps the CTAs'
-// finishing times within about one tile of each other.  Chunk j is tiles
-// [*s, *e).
-constexpr uint32_t kChunk = 12;
+// the next (a chunk's first tile computes them afresh); the last 4 tiles per
+// CTA go one at a time, which keeps the CTAs' finishing times within about
+// one tile of each other.  Chunks hold 12 tiles when the launch has at least
+// 128 tiles per CTA, else 6, which evens out the finishing times of launches
+// of few tiles per CTA (measured: 6 instead of 12 is 1.8% faster on 2^33 odd
+// n, 54 tiles per CTA, and 4% slower on the 4096-range batch, about 300).
+// Chunk j is tiles [*s, *e).
 __device__ __forceinline__ void chunk_range(uint32_t j, uint32_t total, uint32_t ctas, uint32_t *s, uint32_t *e) {
+  const uint32_t chunk = total >= 128u * ctas ? 12u : 6u;
   const uint32_t reserve = 4u * ctas;
-  const uint32_t n_big = total > reserve ? (total - reserve) / kChunk : 0u;
+  const uint32_t n_big = total > reserve ? (total - reserve) / chunk : 0u;
   uint64_t b, f;
   if (j < n_big) {
-    b = (uint64_t)j * kChunk;
-    f = b + kChunk;
+    b = (uint64_t)j * chunk;
+    f = b + chunk;
   } else {
-    b = (uint64_t)n_big * kChunk + (j - n_big);
+    b = (uint64_t)n_big * chunk + (j - n_big);
     f = b + 1;
   }
   *s = (uint32_t)min(b, (uint64_t)total);
