@@ -907,7 +907,14 @@ __global__ void __launch_bounds__(1024, 1) tile_kernel(TileArgs a) {
       for (uint32_t j = S - 1u - tid; j < n_sparse; j += S) {
         const uint32_t q = sh.sparse_q[j];
         uint32_t b = sh.sparse_off[j];
-        for (; b < nbits; b += q) strike(win, b);
+        for (; b + q < nbits; b += 2u * q) {
+          strike(win, b);
+          strike(win, b + q);
+        }
+        if (b < nbits) {
+          strike(win, b);
+          b += q;
+        }
         if (carry) {
           b -= T;
           while (b >= q) b -= q;
