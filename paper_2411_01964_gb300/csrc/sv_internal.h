@@ -230,7 +230,7 @@ cudaError_t build_prime_table(uint64_t pmax, uint32_t **d_p, uint64_t **d_mu, ui
                               uint32_t *n_div, cudaStream_t st);
 
 constexpr int kMaxDensePrimes = 128;  // must match the tile kernel's shared arrays (four warps)
-constexpr int kDenseMinHits = 5;      // primes with at least this many strikes per window are "dense"
+constexpr int kDenseMinHits = 8;      // primes with at least this many strikes per window are "dense"
 constexpr int kMaxSparsePrimes = 2048;  // per-tile primes struck one thread each (shared arrays)
 // Ranges per Barrett item of the bucket fill; a launch of at most this many
 // ranges (one request chunk) has its smallest bucketed primes' hits cut into
