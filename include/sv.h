@@ -434,8 +434,11 @@ sv_status sv_inject_bulk_timeout(sv_ctx *ctx, uint32_t count);
 uint64_t sv_kernel_launches(const sv_ctx *ctx);
 
 /* Per-kernel timing: when enabled, each launch of a timed kernel is
- * bracketed by CUDA events recorded on the stream it is launched on (launches
- * replayed from a captured graph are not timed).  enable: 0 off, -1 every
+ * bracketed by CUDA events recorded on the stream it is launched on.  A
+ * launch replayed from a captured graph times only its tile kernel (id 2),
+ * through event-record nodes given fresh events at every replay; the others
+ * in it are not timed, so sv_launch_range takes the graph path only while no
+ * other kernel is timed.  enable: 0 off, -1 every
  * kernel, otherwise a bit mask of kernel ids (bit i: id i); every call resets
  * the totals.  Kernel ids: 0 init, 1 bucket fill, 2 tile (sieve + scan),
  * 3 stragglers, 4 points, 5 ordered-list compaction, 6 tile kernel of the
