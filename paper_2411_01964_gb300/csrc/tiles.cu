@@ -12,7 +12,8 @@
 //              product of their squares (NS = sv_config.stamp_primes);
 //   2. strike: the next primes up to the bucket threshold clear their odd
 //              multiples of p^2 with shared-memory atomicAnd.  "Dense" primes
-//              (>= 4 hits per window, at most 128) are struck cooperatively:
+//              (>= kDenseMinHits hits per window, at most 128) are struck
+//              cooperatively, two strikes per trip:
 //              the smallest by the whole CTA with a stride of one block, the
 //              others by one warp each with a stride of one warp.  Sparser
 //              ones take one thread per prime.  The offsets of both carry
